@@ -1,0 +1,554 @@
+"""Plain FP64 CPU oracle of the batch-level RGB-Depth-Normal training step.
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, ``__graft_entry__.smoke()`` and
+``bench.py``'s CPU-baseline leg; never by the product path.
+
+What it computes (CityGS-X, Sec. 3.1-3.4), in the paper's order and without
+tiling, blocking or fusion:
+
+1. LoD selection of anchors by observation distance (Sec. 3.1, Octree-GS
+   paragraph), with the cumulative rule ``level <= clamp(floor(log2(d0/d)),
+   0, K-1)``.  No frustum pre-cull: every LoD-active anchor is decoded.
+2. The shared Gaussian decoder F_de (Eq. 4): mu_n = x_v + O_n * l_v and
+   {alpha, c, Sigma} = F_de(F_v, view direction).
+3. EWA projection of every Gaussian (3DGS, cited in Sec. 3.1), the normal as
+   the smallest-scale axis in the camera frame facing the camera (Eq. 6) and
+   the plane distance d = n . mu_c (Eq. 7).
+4. For every pixel centre, all surviving Gaussians of the view in (depth,
+   index) order, blended front to back (Eq. 1 / Eq. 5) into RGB, D and N
+   (Eq. 6-7), then the unbiased depth D_hat = D / (N . K^-1 p~) (Eq. 7).
+5. The batch losses: RGB L1 (Eq. 8), depth L1 against a prior (Eq. 9) and a
+   normal-depth consistency term.
+6. Gradients: reverse-mode differentiation of steps 2-5 by torch.autograd
+   in FP64 (the exact derivative of this definition, not a hand derivation).
+
+Readings of the paper where it is silent (all parameters of ``RenderParams``):
+EWA with 0.3 px^2 dilation and J clamped at 1.3 * tan(fov/2); alpha =
+min(0.99, o * exp(power)); pairs with alpha < 1/255 or power > 0 skipped; a
+pixel stops before the Gaussian that would take T below 1e-4; background 0;
+decoder outputs blocked [alpha x10 | colour x30 | scale x30 | quat x40] with
+sigmoid / sigmoid / l * sigmoid / normalise; quaternions (w, x, y, z).
+
+Besides images and gradients the oracle returns *ambiguity flags*: pixels
+where an FP32 evaluation may legitimately take another branch of one of the
+discrete rules above (a value within rounding of a threshold, or two
+contributing depths within rounding of each other).  Parity tests compare
+only unflagged pixels and report the flagged fraction.
+
+The integer helpers at the end (tile sets, stable sort, exclusive scan, tile
+ranges) are the textbook definitions the GPU's binning and sort must equal.
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+from typing import Dict, List, Optional, Sequence
+
+import numpy as np
+import torch
+
+DT = torch.float64
+N_OFF = 10
+
+
+@dataclasses.dataclass
+class RenderParams:
+    near: float = 0.01
+    dilation: float = 0.3
+    alpha_min: float = 1.0 / 255.0
+    alpha_max: float = 0.99
+    t_min: float = 1e-4
+    jclamp: float = 1.3
+    tile: int = 16
+    tile_pad: float = 1e-3          # padding of the tile-list level set, in ln units
+    lod_d0: float = 1e9
+    n_levels: int = 1
+    bg: float = 0.0
+
+
+@dataclasses.dataclass
+class LossParams:
+    lambda_depth: float = 1.0
+    lambda_normal: float = 0.1
+
+
+def _t(a) -> torch.Tensor:
+    if isinstance(a, torch.Tensor):
+        return a.to(DT)
+    return torch.as_tensor(np.asarray(a), dtype=DT)
+
+
+def camera(cam) -> dict:
+    R = _t(cam.R).reshape(3, 3)
+    t = _t(cam.t).reshape(3)
+    return dict(R=R, t=t, fx=float(cam.fx), fy=float(cam.fy), cx=float(cam.cx), cy=float(cam.cy),
+                W=int(cam.width), H=int(cam.height), center=-(R.T @ t))
+
+
+# ------------------------------------------------------------------ rotations
+def normalize_quat(q: torch.Tensor) -> torch.Tensor:
+    """Unit quaternion; a (near-)zero vector maps to the identity rotation."""
+    n = torch.linalg.norm(q, dim=-1, keepdim=True)
+    ident = torch.zeros_like(q)
+    ident[..., 0] = 1.0
+    small = n < 1e-12
+    return torch.where(small, ident, q / torch.where(small, torch.ones_like(n), n))
+
+
+def quat_to_rotmat(q: torch.Tensor) -> torch.Tensor:
+    """Rotation matrix of a unit quaternion (w, x, y, z); columns are the
+    Gaussian's local axes expressed in world coordinates."""
+    w, x, y, z = q.unbind(-1)
+    R = torch.stack([
+        1 - 2 * (y * y + z * z), 2 * (x * y - w * z), 2 * (x * z + w * y),
+        2 * (x * y + w * z), 1 - 2 * (x * x + z * z), 2 * (y * z - w * x),
+        2 * (x * z - w * y), 2 * (y * z + w * x), 1 - 2 * (x * x + y * y)], -1)
+    return R.reshape(q.shape[:-1] + (3, 3))
+
+
+# ------------------------------------------------------------------ LoD (Sec. 3.1)
+def lod_active(x: torch.Tensor, level: torch.Tensor, cam: dict, rp: RenderParams):
+    """Anchor at level k is active for this camera iff k <= L(d),
+    L(d) = clamp(floor(log2(d0 / d)), 0, K-1), d = |x - camera centre|.
+    Written as comparisons against the exact thresholds d0 / 2^m.
+    Returns (active, ambiguous): ambiguous marks d within 1e-5 relative of a
+    threshold, where an FP32 distance may fall on the other side."""
+    d = torch.linalg.norm(x - cam["center"], dim=-1)
+    L = torch.zeros_like(level)
+    amb = torch.zeros_like(level, dtype=torch.bool)
+    for m in range(1, rp.n_levels):
+        thr = rp.lod_d0 / (2.0 ** m)
+        L = L + (d <= thr).to(level.dtype)
+        amb |= (d - thr).abs() <= 1e-5 * thr
+    return level <= L, amb
+
+
+# ------------------------------------------------------------------ decoder (Eq. 4)
+def decode(anchors: dict, mlp: dict, cam: dict, idx: torch.Tensor, in_dim: int = 35) -> dict:
+    """Decode the anchors ``idx`` into n = 10 neural Gaussians each.
+
+    Input X = [F_v (32), unit direction (x_v - o_c)/|.| (3)] (+ distance if
+    ``in_dim`` = 36); H = ReLU(W1 X + b1); Z = W2 H + b2 (110)."""
+    x = anchors["x"][idx]
+    F = anchors["feat"][idx]
+    l = torch.exp(anchors["log_l"][idx])
+    O = anchors["offsets"][idx]
+    dvec = x - cam["center"]
+    dist = torch.linalg.norm(dvec, dim=-1, keepdim=True)
+    parts = [F, dvec / dist]
+    if in_dim == 36:
+        parts.append(dist)
+    X = torch.cat(parts, -1)
+    H = torch.relu(X @ mlp["W1"].T + mlp["b1"])
+    Z = H @ mlp["W2"].T + mlp["b2"]
+    A = x.shape[0]
+    opacity = torch.sigmoid(Z[:, 0:10])
+    color = torch.sigmoid(Z[:, 10:40]).reshape(A, N_OFF, 3)
+    scale = l[:, None, :] * torch.sigmoid(Z[:, 40:70]).reshape(A, N_OFF, 3)
+    quat = normalize_quat(Z[:, 70:110].reshape(A, N_OFF, 4))
+    mu = x[:, None, :] + O * l[:, None, :]
+    return dict(mu=mu.reshape(-1, 3), opacity=opacity.reshape(-1), color=color.reshape(-1, 3),
+                scale=scale.reshape(-1, 3), quat=quat.reshape(-1, 4), X=X, H=H, Z=Z)
+
+
+# ------------------------------------------------------------------ projection
+def project(mu, scale, quat, opacity, color, cam: dict, rp: RenderParams) -> dict:
+    """EWA splatting of 3D Gaussians (3DGS): 2D mean, 2D covariance with
+    dilation, its inverse (conic), view depth z, camera-frame normal facing
+    the camera (Eq. 6 reading) and plane distance d = n . mu_c (Eq. 7)."""
+    R, t = cam["R"], cam["t"]
+    fx, fy, cx, cy, W, H = cam["fx"], cam["fy"], cam["cx"], cam["cy"], cam["W"], cam["H"]
+    mu_c = mu @ R.T + t
+    x, y, z = mu_c.unbind(-1)
+    lim_x = rp.jclamp * 0.5 * W / fx
+    lim_y = rp.jclamp * 0.5 * H / fy
+    txz = torch.clamp(x / z, -lim_x, lim_x)
+    tyz = torch.clamp(y / z, -lim_y, lim_y)
+    zero = torch.zeros_like(z)
+    J = torch.stack([torch.stack([fx / z, zero, -fx * txz / z], -1),
+                     torch.stack([zero, fy / z, -fy * tyz / z], -1)], -2)        # [G,2,3]
+    Rg = quat_to_rotmat(quat)                                                     # [G,3,3]
+    M = Rg * scale[:, None, :]
+    Sigma = M @ M.transpose(-1, -2)
+    T = J @ R
+    cov = T @ Sigma @ T.transpose(-1, -2)
+    a = cov[:, 0, 0] + rp.dilation
+    b = cov[:, 0, 1]
+    c = cov[:, 1, 1] + rp.dilation
+    det = a * c - b * b
+    conic = torch.stack([c / det, -b / det, a / det], -1)
+    mean2d = torch.stack([fx * x / z + cx, fy * y / z + cy], -1)
+    k = torch.argmin(scale.detach(), dim=-1)                                     # first minimum on ties
+    n_w = torch.gather(Rg, 2, k[:, None, None].expand(-1, 3, 1))[..., 0]
+    n_c = n_w @ R.T
+    facing = (n_c * mu_c).sum(-1)
+    sgn = torch.where(facing.detach() > 0, -torch.ones_like(facing), torch.ones_like(facing))
+    n_c = n_c * sgn[:, None]
+    dist = (n_c * mu_c).sum(-1)
+    valid = (z.detach() >= rp.near) & (det.detach() > 0) & (opacity.detach() >= rp.alpha_min)
+    with torch.no_grad():
+        s_sorted = torch.sort(scale, dim=-1).values
+        amb = ((z - rp.near).abs() <= 1e-5 * rp.near)
+        amb |= facing.abs() <= 1e-5 * torch.linalg.norm(mu_c, dim=-1)
+        amb |= (s_sorted[:, 1] - s_sorted[:, 0]) <= 1e-5 * s_sorted[:, 1]
+        amb |= (opacity - rp.alpha_min).abs() <= 1e-5 * rp.alpha_min
+    return dict(mean2d=mean2d, cov=torch.stack([a, b, c], -1), conic=conic, z=z, normal=n_c,
+                dist=dist, opacity=opacity, color=color, valid=valid, ambiguous=amb, mu_c=mu_c)
+
+
+# ------------------------------------------------------------------ blending (Eq. 1, 5-7)
+def _reject_rect(proj: dict, keep: torch.Tensor, x0, x1, y0, y1, rp: RenderParams) -> torch.Tensor:
+    """Gaussians that can reach alpha >= alpha_min somewhere in the pixel-centre
+    rectangle [x0,x1]x[y0,y1].  Provable bound: power <= -|delta|^2 /
+    (2 lambda_max(cov)), so o * exp(that) < alpha_min (with a 1e-6 margin)
+    rules the Gaussian out everywhere in the rectangle."""
+    with torch.no_grad():
+        m = proj["mean2d"]
+        a, b, c = proj["cov"].unbind(-1)
+        lam = 0.5 * (a + c) + torch.sqrt(torch.clamp(0.25 * (a - c) ** 2 + b * b, min=0.0))
+        ddx = torch.clamp(torch.maximum(x0 - m[:, 0], m[:, 0] - x1), min=0.0)
+        ddy = torch.clamp(torch.maximum(y0 - m[:, 1], m[:, 1] - y1), min=0.0)
+        bound = proj["opacity"] * torch.exp(-0.5 * (ddx * ddx + ddy * ddy) / lam)
+        return keep & (bound >= rp.alpha_min * (1.0 - 1e-6))
+
+
+def blend_pixels(proj: dict, order: torch.Tensor, px: torch.Tensor, py: torch.Tensor, rp: RenderParams,
+                 cam: dict) -> dict:
+    """Front-to-back compositing of the Gaussians ``order`` (already sorted by
+    depth, index) at pixel centres (px, py).  Eq. 5 (RGB), Eq. 6 (normal),
+    Eq. 7 (distance D and unbiased depth D_hat)."""
+    m = proj["mean2d"][order]
+    A, B, C = proj["conic"][order].unbind(-1)
+    o = proj["opacity"][order]
+    col = proj["color"][order]
+    d = proj["dist"][order]
+    n = proj["normal"][order]
+    dx = px[:, None] - m[None, :, 0]
+    dy = py[:, None] - m[None, :, 1]
+    power = -0.5 * (A * dx * dx + C * dy * dy) - B * dx * dy
+    a_raw = o * torch.exp(power)
+    skip = (power.detach() > 0) | (a_raw.detach() < rp.alpha_min)
+    alpha = torch.where(skip, torch.zeros_like(a_raw), torch.clamp(a_raw, max=rp.alpha_max))
+    om = 1.0 - alpha
+    T_incl = torch.cumprod(om, dim=1)
+    T_excl = torch.cat([torch.ones_like(T_incl[:, :1]), T_incl[:, :-1]], 1)
+    included = (T_incl.detach() >= rp.t_min)
+    w = alpha * T_excl * included
+    rgb = w @ col if w.shape[1] else torch.zeros(px.shape[0], 3, dtype=DT)
+    D = w @ d if w.shape[1] else torch.zeros(px.shape[0], dtype=DT)
+    N = w @ n if w.shape[1] else torch.zeros(px.shape[0], 3, dtype=DT)
+    T_final = torch.prod(torch.where(included, om, torch.ones_like(om)), dim=1)
+    rgb = rgb + T_final[:, None] * rp.bg
+    # Eq. 7: D_hat = D / (N . K^-1 p~), guarded [reading]
+    r = torch.stack([(px - cam["cx"]) / cam["fx"], (py - cam["cy"]) / cam["fy"], torch.ones_like(px)], -1)
+    ndr = (N * r).sum(-1)
+    ok = (ndr.detach().abs() >= 1e-8) & ((1.0 - T_final.detach()) >= 1e-6)
+    depth = torch.where(ok, D / torch.where(ok, ndr, torch.ones_like(ndr)), torch.zeros_like(D))
+    with torch.no_grad():
+        contrib = included & ~skip
+        n_contrib = contrib.sum(1)
+        evaluated = T_excl >= rp.t_min
+        ev_ns = evaluated & ~skip
+        flag = ((a_raw - rp.alpha_min).abs() <= 1e-4 * rp.alpha_min) & evaluated
+        flag |= ((a_raw - rp.alpha_max).abs() <= 1e-4 * rp.alpha_max) & evaluated
+        flag |= ((T_incl - rp.t_min).abs() <= 1e-3 * rp.t_min) & ev_ns
+        flag |= proj["ambiguous"][order][None, :] & ev_ns
+        pix_flag = flag.any(1)
+        # near-equal depths among contributors (order may differ in FP32)
+        zz = proj["z"][order]
+        big = contrib & (w.detach() > 1e-7)
+        G = big.shape[1]
+        pos = torch.where(big, torch.arange(G)[None, :].expand_as(big), torch.full_like(big, -1, dtype=torch.long))
+        prev = torch.cummax(torch.cat([torch.full_like(pos[:, :1], -1), pos[:, :-1]], 1), dim=1).values
+        has_prev = big & (prev >= 0)
+        zprev = zz[prev.clamp(min=0)]
+        tie = has_prev & ((zz[None, :] - zprev).abs() <= 1e-5 * zz[None, :])
+        pix_flag |= tie.any(1)
+        pix_flag |= ((1.0 - T_final - 1e-6).abs() <= 1e-3 * 1e-6)
+        pix_flag |= ((ndr.abs() - 1e-8).abs() <= 0.5e-8)
+    return dict(rgb=rgb, D=D, normal=N, depth=depth, T_final=T_final, n_contrib=n_contrib, flag=pix_flag)
+
+
+def sort_order(proj: dict, keep: torch.Tensor) -> torch.Tensor:
+    """Surviving Gaussians ordered by (view depth z, Gaussian index)."""
+    idx = torch.nonzero(keep).flatten()
+    z = proj["z"].detach()[idx]
+    perm = torch.sort(z, stable=True).indices
+    return idx[perm]
+
+
+def render_view(proj: dict, cam: dict, rp: RenderParams, crop=None, block: int = 32,
+                image_grads: Optional[dict] = None) -> dict:
+    """Render one view (or the crop (x0, y0, w, h)) pixel by pixel.
+
+    Pixels are processed in independent blocks only to bound memory; each
+    block sees every surviving Gaussian that can reach alpha >= alpha_min in
+    it.  If ``image_grads`` (dL/d rgb, depth, normal over the crop) is given,
+    the vector-Jacobian product is accumulated into the leaves' ``.grad``."""
+    W, H = cam["W"], cam["H"]
+    x0, y0, w, h = crop if crop is not None else (0, 0, W, H)
+    keep_all = proj["valid"] | proj["ambiguous"]
+    out = {k: torch.zeros(sh, dtype=DT) for k, sh in
+           dict(rgb=(3, h, w), depth=(h, w), normal=(3, h, w), D=(h, w), T_final=(h, w)).items()}
+    out["n_contrib"] = torch.zeros(h, w, dtype=torch.long)
+    out["flag"] = torch.zeros(h, w, dtype=torch.bool)
+    valid_order = sort_order(proj, proj["valid"])
+    amb_only = proj["ambiguous"] & ~proj["valid"]
+    for by in range(0, h, block):
+        for bx in range(0, w, block):
+            bh, bw = min(block, h - by), min(block, w - bx)
+            ys = torch.arange(y0 + by, y0 + by + bh, dtype=DT) + 0.5
+            xs = torch.arange(x0 + bx, x0 + bx + bw, dtype=DT) + 0.5
+            PY, PX = torch.meshgrid(ys, xs, indexing="ij")
+            px, py = PX.reshape(-1), PY.reshape(-1)
+            near = _reject_rect(proj, keep_all, xs[0], xs[-1], ys[0], ys[-1], rp)
+            order = valid_order[near[valid_order]]
+            res = blend_pixels(proj, order, px, py, rp, cam)
+            # an ambiguous Gaussian the oracle culled may still be kept in FP32
+            amb_idx = torch.nonzero(amb_only & near).flatten()
+            if amb_idx.numel():
+                with torch.no_grad():
+                    m = proj["mean2d"][amb_idx]
+                    A, B, C = proj["conic"][amb_idx].unbind(-1)
+                    ddx = px[:, None] - m[None, :, 0]
+                    ddy = py[:, None] - m[None, :, 1]
+                    pw = -0.5 * (A * ddx * ddx + C * ddy * ddy) - B * ddx * ddy
+                    hit = (proj["opacity"][amb_idx] * torch.exp(pw) >= rp.alpha_min * 0.5).any(1)
+                    res["flag"] = res["flag"] | hit
+            sl = (slice(by, by + bh), slice(bx, bx + bw))
+            if image_grads is not None:
+                g_rgb = image_grads["rgb"][:, sl[0], sl[1]].reshape(3, -1).T
+                g_d = image_grads["depth"][sl].reshape(-1)
+                g_n = image_grads["normal"][:, sl[0], sl[1]].reshape(3, -1).T
+                tot = (res["rgb"] * g_rgb).sum() + (res["depth"] * g_d).sum() + (res["normal"] * g_n).sum()
+                if tot.requires_grad:
+                    tot.backward(retain_graph=True)
+            out["rgb"][:, sl[0], sl[1]] = res["rgb"].detach().T.reshape(3, bh, bw)
+            out["normal"][:, sl[0], sl[1]] = res["normal"].detach().T.reshape(3, bh, bw)
+            for k in ("depth", "D", "T_final", "n_contrib", "flag"):
+                out[k][sl] = res[k].detach().reshape(bh, bw)
+    return out
+
+
+# ------------------------------------------------------------------ full step
+def leaves_explicit(scene: dict) -> dict:
+    return {k: _t(scene[k]).clone().requires_grad_(True)
+            for k in ("means", "log_scales", "quats", "opacity_logits", "colors")}
+
+
+def leaves_anchor(scene: dict) -> dict:
+    p = {k: _t(scene[k]).clone().requires_grad_(True) for k in ("x", "log_l", "offsets", "feat")}
+    for k, v in scene["mlp"].items():
+        p[k] = _t(v).clone().requires_grad_(True)
+    return p
+
+
+def gaussians_for_view(scene: dict, leaves: dict, cam: dict, rp: RenderParams, in_dim: int = 35,
+                       exclude: Optional[torch.Tensor] = None) -> dict:
+    """Per-view 3D Gaussians: explicit ones as given, or the decoded ones of
+    every LoD-active anchor (Eq. 4).  Index = anchor * 10 + j."""
+    if scene["kind"] == "explicit":
+        return dict(mu=leaves["means"], scale=torch.exp(leaves["log_scales"]),
+                    quat=normalize_quat(leaves["quats"]), opacity=torch.sigmoid(leaves["opacity_logits"]),
+                    color=leaves["colors"], lod_amb=None)
+    level = torch.as_tensor(np.asarray(scene["level"]), dtype=torch.long)
+    active, amb = lod_active(leaves["x"].detach(), level, cam, rp)
+    if exclude is not None:
+        active &= ~exclude
+    idx = torch.nonzero(active).flatten()
+    anchors = dict(x=leaves["x"], feat=leaves["feat"], log_l=leaves["log_l"], offsets=leaves["offsets"])
+    mlp = {k: leaves[k] for k in ("W1", "b1", "W2", "b2")}
+    dec = decode(anchors, mlp, cam, idx, in_dim)
+    dec["anchor_idx"] = idx
+    dec["lod_amb"] = amb
+    return dec
+
+
+def render(scene: dict, rp: RenderParams, leaves: Optional[dict] = None, crops=None,
+           image_grads: Optional[Sequence[dict]] = None, views: Optional[Sequence[int]] = None,
+           exclude: Optional[torch.Tensor] = None, block: int = 32, in_dim: int = 35) -> dict:
+    """Render every view (optionally a crop per view).  With ``image_grads``
+    the VJP lands in ``leaves[*].grad``.  Returns per-view dicts."""
+    if leaves is None:
+        leaves = leaves_explicit(scene) if scene["kind"] == "explicit" else leaves_anchor(scene)
+    views = list(range(len(scene["cameras"]))) if views is None else list(views)
+    outs = []
+    for v in views:
+        cam = camera(scene["cameras"][v])
+        g = gaussians_for_view(scene, leaves, cam, rp, in_dim, exclude)
+        proj = project(g["mu"], g["scale"], g["quat"], g["opacity"], g["color"], cam, rp)
+        crop = crops[v] if crops is not None else None
+        ig = image_grads[v] if image_grads is not None else None
+        if ig is not None:
+            ig = {k: _t(val) for k, val in ig.items()}
+        out = render_view(proj, cam, rp, crop, block, ig)
+        out["n_gaussians"] = int(proj["valid"].sum())
+        out["proj"] = {k: (val.detach() if isinstance(val, torch.Tensor) else val) for k, val in proj.items()}
+        out["lod_amb"] = g.get("lod_amb")
+        out["anchor_idx"] = g.get("anchor_idx")
+        outs.append(out)
+    return dict(views=outs, leaves=leaves)
+
+
+# ------------------------------------------------------------------ losses (Eq. 8-9 + consistency)
+def depth_normal(depth: torch.Tensor, cam: dict):
+    """Normal of the surface implied by a depth map: back-project pixel
+    centres P = D_hat * K^-1 [u+.5, v+.5, 1], cross product of the central
+    differences along x and y, normalised and turned to face the camera.
+    Returns (normal [3,H,W], valid [H,W]) -- valid needs an interior pixel
+    with positive depth at itself and its four neighbours."""
+    H, W = depth.shape
+    v, u = torch.meshgrid(torch.arange(H, dtype=DT) + 0.5, torch.arange(W, dtype=DT) + 0.5, indexing="ij")
+    r = torch.stack([(u - cam["cx"]) / cam["fx"], (v - cam["cy"]) / cam["fy"], torch.ones_like(u)], 0)
+    P = depth[None] * r
+    Nd = torch.zeros(3, H, W, dtype=DT)
+    valid = torch.zeros(H, W, dtype=torch.bool)
+    if H >= 3 and W >= 3:
+        ex = P[:, 1:-1, 2:] - P[:, 1:-1, :-2]
+        ey = P[:, 2:, 1:-1] - P[:, :-2, 1:-1]
+        cr = torch.cross(ex, ey, dim=0)
+        nrm = torch.linalg.norm(cr, dim=0)
+        pos = depth > 0
+        ok = pos[1:-1, 1:-1] & pos[1:-1, 2:] & pos[1:-1, :-2] & pos[2:, 1:-1] & pos[:-2, 1:-1] & (nrm > 1e-20)
+        nd = cr / torch.where(nrm > 0, nrm, torch.ones_like(nrm))
+        face = (nd * P[:, 1:-1, 1:-1]).sum(0)
+        nd = torch.where(face > 0, -nd, nd)
+        Nd[:, 1:-1, 1:-1] = nd
+        valid[1:-1, 1:-1] = ok
+    return Nd, valid
+
+
+def loss_view(rgb, depth, normal, target: dict, cam: dict, lp: LossParams) -> dict:
+    """Per-view loss terms (before the 1/B batch mean):
+    RGB L1 mean over pixels and channels (Eq. 8); depth L1 over the prior's
+    mask, normalised by the mask count (Eq. 9); normal-depth consistency
+    mean(1 - N_d . N/|N|) over valid pixels with N_d under stop-gradient."""
+    I = _t(target["rgb"])
+    prior = _t(target["prior"])
+    mask = _t(target["mask"])
+    l_rgb = (rgb - I).abs().mean()
+    l_depth = (mask * (depth - prior).abs()).sum() / torch.clamp(mask.sum(), min=1.0)
+    with torch.no_grad():
+        Nd, valid = depth_normal(depth.detach(), cam)
+    nn_ = torch.linalg.norm(normal, dim=0)
+    valid = valid & (nn_.detach() > 1e-8)
+    cosang = (Nd * normal).sum(0) / torch.where(valid, nn_, torch.ones_like(nn_))
+    cnt = max(int(valid.sum()), 1)
+    l_normal = torch.where(valid, 1.0 - cosang, torch.zeros_like(cosang)).sum() / cnt
+    total = l_rgb + lp.lambda_depth * l_depth + lp.lambda_normal * l_normal
+    return dict(total=total, rgb=l_rgb, depth=l_depth, normal=l_normal, n_valid=int(valid.sum()))
+
+
+def batch_loss(maps: Sequence[dict], targets: Sequence[dict], cams: Sequence, lp: LossParams) -> dict:
+    """L = (1/B) sum_b [L_rgb + lambda_d L_depth + lambda_n L_normal]."""
+    B = len(maps)
+    terms = [loss_view(m["rgb"], m["depth"], m["normal"], t, camera(c), lp) for m, t, c in zip(maps, targets, cams)]
+    total = sum(t["total"] for t in terms) / B
+    return dict(total=total, terms=terms)
+
+
+def loss_and_image_grads(maps: Sequence[dict], targets: Sequence[dict], cams: Sequence, lp: LossParams):
+    """Loss value and dL/d(rgb, depth, normal) per view (FP64 autograd)."""
+    leaves = [{k: _t(m[k]).clone().requires_grad_(True) for k in ("rgb", "depth", "normal")} for m in maps]
+    L = batch_loss(leaves, targets, cams, lp)
+    L["total"].backward()
+    grads = [{k: lv[k].grad.detach().clone() for k in lv} for lv in leaves]
+    return float(L["total"]), grads, L
+
+
+def loss_ambiguity(maps: Sequence[dict], targets: Sequence[dict], tol: float = 1e-5):
+    """Pixels where the sign of an L1 residual is decided within rounding."""
+    flags = []
+    for m, t in zip(maps, targets):
+        f = ((_t(m["rgb"]) - _t(t["rgb"])).abs() <= tol).any(0)
+        f |= ((_t(m["depth"]) - _t(t["prior"])).abs() <= tol) & (_t(t["mask"]) > 0)
+        flags.append(f)
+    return flags
+
+
+# ------------------------------------------------------------------ integer definitions
+def tile_set(mean2d, conic, opacity, W: int, H: int, rp: RenderParams, margin: float = 0.0):
+    """Tiles of one view whose pixel-centre rectangle meets the level set
+    1/2 delta^T Q delta <= ln(255 * o) + pad of a Gaussian (the set on which
+    alpha >= 1/255, padded in the exponent).  Decided by the exact minimum of
+    the quadratic over the rectangle (convex: the unconstrained minimiser if
+    inside, else the best point of the four edges).
+
+    Returns (tiles, ambiguous) as python lists of global-in-view tile ids;
+    ``ambiguous`` holds tiles whose minimum lies within ``margin`` (relative)
+    of the level."""
+    tile = rp.tile
+    tx_n, ty_n = (W + tile - 1) // tile, (H + tile - 1) // tile
+    mx, my = float(mean2d[0]), float(mean2d[1])
+    A, B, C = (float(v) for v in conic)
+    o = float(opacity)
+    if o < rp.alpha_min:
+        return [], []
+    lvl = math.log(255.0 * o) + rp.tile_pad
+    det = A * C - B * B
+    cov_xx, cov_yy = C / det, A / det
+    rx = math.sqrt(max(2.0 * lvl * cov_xx, 0.0)) * (1 + 4 * margin) + 1e-9
+    ry = math.sqrt(max(2.0 * lvl * cov_yy, 0.0)) * (1 + 4 * margin) + 1e-9
+
+    def q(dx, dy):
+        return A * dx * dx + 2 * B * dx * dy + C * dy * dy
+
+    def seg_min_v(dx, lo, hi):                      # edge with fixed dx, dy in [lo, hi]
+        dy = -B * dx / C
+        dy = min(max(dy, lo), hi)
+        return q(dx, dy)
+
+    def seg_min_h(dy, lo, hi):
+        dx = -B * dy / A
+        dx = min(max(dx, lo), hi)
+        return q(dx, dy)
+
+    tiles, amb = [], []
+    t0x = max(0, int(math.floor((mx - rx - 0.5) / tile)))
+    t1x = min(tx_n - 1, int(math.floor((mx + rx - 0.5) / tile)))
+    t0y = max(0, int(math.floor((my - ry - 0.5) / tile)))
+    t1y = min(ty_n - 1, int(math.floor((my + ry - 0.5) / tile)))
+    for ty in range(t0y, t1y + 1):
+        y0 = ty * tile + 0.5 - my
+        y1 = min(ty * tile + tile - 0.5, H - 0.5) - my
+        for tx in range(t0x, t1x + 1):
+            x0 = tx * tile + 0.5 - mx
+            x1 = min(tx * tile + tile - 0.5, W - 0.5) - mx
+            if x0 <= 0 <= x1 and y0 <= 0 <= y1:
+                mn = 0.0
+            else:
+                mn = min(seg_min_v(x0, y0, y1), seg_min_v(x1, y0, y1), seg_min_h(y0, x0, x1), seg_min_h(y1, x0, x1))
+            val = 0.5 * mn
+            if val <= lvl:
+                tiles.append(ty * tx_n + tx)
+            if abs(val - lvl) <= margin * max(lvl, 1.0):
+                amb.append(ty * tx_n + tx)
+    return tiles, amb
+
+
+def exclusive_scan(counts: np.ndarray) -> np.ndarray:
+    counts = np.asarray(counts, dtype=np.uint64)
+    out = np.zeros_like(counts)
+    if len(counts) > 1:
+        out[1:] = np.cumsum(counts[:-1])
+    return out
+
+
+def stable_sort(keys: np.ndarray, values: np.ndarray):
+    perm = np.argsort(keys, kind="stable")
+    return keys[perm], values[perm]
+
+
+def tile_ranges(sorted_tiles: np.ndarray, n_tiles: int) -> np.ndarray:
+    """ranges[t] = [first, last+1) of tile t in the sorted list, [0,0) if absent."""
+    r = np.zeros((n_tiles, 2), dtype=np.int64)
+    prev = None
+    for i, t in enumerate(sorted_tiles.tolist()):
+        if t != prev:
+            r[t, 0] = i
+            if prev is not None:
+                r[prev, 1] = i
+            prev = t
+    if prev is not None:
+        r[prev, 1] = len(sorted_tiles)
+    return r
