@@ -49,6 +49,12 @@ import torch
 
 DT = torch.float64
 N_OFF = 10
+# Relative reach of an FP32 evaluation around the alpha thresholds, the
+# transmittance stop and the per-Gaussian discrete choices: pixels with a
+# decision inside it are flagged ambiguous.
+AMB_ALPHA = 5e-5
+AMB_T = 1e-4
+AMB_GAUSS = 2e-6
 
 
 @dataclasses.dataclass
@@ -187,13 +193,22 @@ def project(mu, scale, quat, opacity, color, cam: dict, rp: RenderParams) -> dic
     dist = (n_c * mu_c).sum(-1)
     valid = (z.detach() >= rp.near) & (det.detach() > 0) & (opacity.detach() >= rp.alpha_min)
     with torch.no_grad():
+        zd = z.detach()
+        z32 = zd.to(torch.float32)
+        zkey = z32.to(DT)
+        zulp = torch.from_numpy(np.spacing(np.abs(z32.numpy())).astype(np.float64))
+        # exact depth within 1e-9 (relative) of the midpoint between two FP32 values
+        zmid = ((zd - zkey).abs() - 0.5 * zulp).abs() <= 1e-9 * zd.abs()
         s_sorted = torch.sort(scale, dim=-1).values
+        # Gaussian-level decisions within FP32 reach: near plane, the facing
+        # flip of the normal (edge-on), the smallest-scale axis (near ties)
         amb = ((z - rp.near).abs() <= 1e-5 * rp.near)
-        amb |= facing.abs() <= 1e-5 * torch.linalg.norm(mu_c, dim=-1)
-        amb |= (s_sorted[:, 1] - s_sorted[:, 0]) <= 1e-5 * s_sorted[:, 1]
+        amb |= facing.abs() <= AMB_GAUSS * torch.linalg.norm(mu_c, dim=-1)
+        amb |= (s_sorted[:, 1] - s_sorted[:, 0]) <= AMB_GAUSS * s_sorted[:, 1]
         amb |= (opacity - rp.alpha_min).abs() <= 1e-5 * rp.alpha_min
     return dict(mean2d=mean2d, cov=torch.stack([a, b, c], -1), conic=conic, z=z, normal=n_c,
-                dist=dist, opacity=opacity, color=color, valid=valid, ambiguous=amb, mu_c=mu_c)
+                dist=dist, opacity=opacity, color=color, valid=valid, ambiguous=amb, mu_c=mu_c,
+                zkey=zkey, zulp=zulp, zmid=zmid)
 
 
 # ------------------------------------------------------------------ blending (Eq. 1, 5-7)
@@ -249,20 +264,24 @@ def blend_pixels(proj: dict, order: torch.Tensor, px: torch.Tensor, py: torch.Te
         n_contrib = contrib.sum(1)
         evaluated = T_excl >= rp.t_min
         ev_ns = evaluated & ~skip
-        flag = ((a_raw - rp.alpha_min).abs() <= 1e-4 * rp.alpha_min) & evaluated
-        flag |= ((a_raw - rp.alpha_max).abs() <= 1e-4 * rp.alpha_max) & evaluated
-        flag |= ((T_incl - rp.t_min).abs() <= 1e-3 * rp.t_min) & ev_ns
+        # a decision within the FP32 evaluation's reach of its threshold
+        flag = ((a_raw - rp.alpha_min).abs() <= AMB_ALPHA * rp.alpha_min) & evaluated
+        flag |= ((a_raw - rp.alpha_max).abs() <= AMB_ALPHA * rp.alpha_max) & evaluated
+        flag |= ((T_incl - rp.t_min).abs() <= AMB_T * rp.t_min) & ev_ns
         flag |= proj["ambiguous"][order][None, :] & ev_ns
         pix_flag = flag.any(1)
-        # near-equal depths among contributors (order may differ in FP32)
-        zz = proj["z"][order]
+        # two contributors whose FP32 depth keys are adjacent while one exact
+        # depth sits within rounding of an FP32 midpoint: either order is valid
+        key = proj["zkey"][order]
+        mid = proj["zmid"][order]
         big = contrib & (w.detach() > 1e-7)
         G = big.shape[1]
         pos = torch.where(big, torch.arange(G)[None, :].expand_as(big), torch.full_like(big, -1, dtype=torch.long))
         prev = torch.cummax(torch.cat([torch.full_like(pos[:, :1], -1), pos[:, :-1]], 1), dim=1).values
         has_prev = big & (prev >= 0)
-        zprev = zz[prev.clamp(min=0)]
-        tie = has_prev & ((zz[None, :] - zprev).abs() <= 1e-5 * zz[None, :])
+        pc = prev.clamp(min=0)
+        close = (key[None, :] - key[pc]).abs() <= 1.5 * proj["zulp"][order][None, :]
+        tie = has_prev & close & (mid[None, :] | mid[pc])
         pix_flag |= tie.any(1)
         pix_flag |= ((1.0 - T_final - 1e-6).abs() <= 1e-3 * 1e-6)
         pix_flag |= ((ndr.abs() - 1e-8).abs() <= 0.5e-8)
@@ -270,9 +289,12 @@ def blend_pixels(proj: dict, order: torch.Tensor, px: torch.Tensor, py: torch.Te
 
 
 def sort_order(proj: dict, keep: torch.Tensor) -> torch.Tensor:
-    """Surviving Gaussians ordered by (view depth z, Gaussian index)."""
+    """Surviving Gaussians ordered by (view depth z as an FP32 key, Gaussian
+    index).  The paper leaves the key's precision open; the order is an
+    integer decision taken from a float, so it is taken in the kernel's
+    precision: z rounded to the nearest FP32 value, ties by index."""
     idx = torch.nonzero(keep).flatten()
-    z = proj["z"].detach()[idx]
+    z = proj["zkey"][idx]
     perm = torch.sort(z, stable=True).indices
     return idx[perm]
 
