@@ -1,0 +1,283 @@
+/*
+ * pgs.h -- C ABI of the single-GPU (sm_103a) hot path of the batch-level
+ * RGB-Depth-Normal training step over the hybrid anchor / voxel Gaussian
+ * representation (PH^2-3D) of CityGS-X.
+ *
+ * The step is: LoD + frustum cull of anchors (Sec. 3.1, Octree-GS paragraph)
+ * -> shared decoder F_de turning each visible anchor into n = 10 Gaussians
+ * (Eq. 4) -> EWA projection -> tile binning and a radix sort by (tile, depth)
+ * (the reorder pi of Eq. 5) -> front-to-back blending of RGB (Eq. 5), normal
+ * (Eq. 6) and distance / unbiased depth (Eq. 7) -> batch losses (Eq. 8-9 plus
+ * a normal-depth consistency term) -> reverse-order backward to the anchor
+ * and decoder parameters.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Every pointer named d_* or held in a *_ptrs struct is a DEVICE pointer
+ *    owned by the caller; the library never frees it.  The library owns only
+ *    its workspace, allocated in pgs_scene_create and freed in
+ *    pgs_scene_destroy.  Host pointers (descriptors, camera arrays) are read
+ *    during the call only.
+ *  - Cameras: OpenCV frame (x right, y down, z forward); R maps world to
+ *    camera (row-major 3x3), x_cam = R x_world + t; pixel centres sit at
+ *    (u + 0.5, v + 0.5).
+ *  - Images of a batch live in one ragged arena: view v occupies pixels
+ *    [pix_off[v], pix_off[v] + W_v H_v) with pix_off[v] = sum_{u<v} W_u H_u.
+ *    Single-channel maps are [pix] (row-major H x W per view); 3-channel maps
+ *    are planar per view: channel c of view v starts at 3 pix_off[v] + c W_v H_v.
+ *  - Gradient outputs are ACCUMULATED into (+=); the caller zeroes them.
+ *  - Calls that take a cudaStream_t only enqueue work on it: they never
+ *    synchronise, allocate or read back, so a sequence of them can be captured
+ *    into a CUDA graph.  Argument errors are returned at once; errors found by
+ *    the GPU (capacity overflow, a bounded wait that ran out, non-finite
+ *    values) raise a device flag that pgs_read_status returns.
+ *  - Status codes: PGS_OK = 0, otherwise one of pgs_status_code; the message
+ *    of the last failing call on this host thread is pgs_last_error().
+ */
+#ifndef PGS_H_
+#define PGS_H_
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int pgs_status;
+enum pgs_status_code {
+  PGS_OK = 0,
+  PGS_ERR_INVALID_ARG = 1,   /* bad pointer, size or descriptor field */
+  PGS_ERR_CAPACITY = 2,      /* rows / pairs exceeded the capacities given at create */
+  PGS_ERR_TIMEOUT = 3,       /* a bounded device-side wait (sort look-back) ran out */
+  PGS_ERR_NONFINITE = 4,     /* non-finite value met in a loss or gradient */
+  PGS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
+  PGS_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
+};
+
+#define PGS_MAX_VIEWS 32
+#define PGS_N_OFFSETS 10
+#define PGS_FEAT_DIM 32
+#define PGS_HIDDEN 32
+#define PGS_OUT_DIM 110
+
+enum pgs_mode { PGS_MODE_EXPLICIT = 0, PGS_MODE_ANCHOR = 1 };
+enum pgs_decode_precision { PGS_DECODE_FP32 = 0, PGS_DECODE_BF16 = 1 };
+
+typedef struct pgs_camera {
+  float R[9];        /* world -> camera rotation, row-major */
+  float t[3];        /* translation, x_cam = R x_world + t */
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} pgs_camera;
+
+/* Thresholds of the blending rules (3DGS, which Sec. 3.1 builds on) and of
+ * the LoD rule (Sec. 3.1).  pgs_default_params fills the values the library
+ * is tested with: near 0.01, dilation 0.3 px^2, alpha in [1/255, 0.99], stop
+ * before T drops below 1e-4, J clamp 1.3 tan(fov/2), tile-list pad 1e-3, bg 0. */
+typedef struct pgs_render_params {
+  float near_plane;
+  float dilation;
+  float alpha_min;
+  float alpha_max;
+  float t_min;
+  float jclamp;
+  float tile_pad;      /* the tile list of a Gaussian is its ln(255 o) + tile_pad level set */
+  float lod_d0;        /* anchor at level k active iff k <= clamp(floor(log2(d0/d)), 0, K-1) */
+  int32_t n_levels;    /* K */
+  float bg;            /* background value of the RGB channels (depth / normal have none) */
+  int32_t tile_w;      /* 16 x 16 default; 8 x 32 and 32 x 8 also accepted */
+  int32_t tile_h;
+  int32_t decode_precision;   /* pgs_decode_precision (anchor mode) */
+  int32_t in_dim;      /* decoder input: 35 = feature + unit view direction (36 adds distance) */
+} pgs_render_params;
+
+typedef struct pgs_scene_desc {
+  int32_t mode;                 /* pgs_mode */
+  int64_t n_primitives;         /* explicit: Gaussians; anchor: anchors (< 2^27) */
+  int32_t max_views;            /* <= PGS_MAX_VIEWS */
+  int64_t max_pixels;           /* sum of W_v H_v over a batch */
+  int64_t capacity_rows;        /* anchor mode: visible (view, anchor) rows */
+  int64_t capacity_pairs;       /* (Gaussian-view, tile) pairs, < 2^30 */
+  pgs_render_params params;
+} pgs_scene_desc;
+
+typedef struct pgs_explicit_ptrs {   /* N Gaussians, float32, caller-owned */
+  const float* means;           /* [N,3] world */
+  const float* log_scales;      /* [N,3] */
+  const float* quats;           /* [N,4] (w,x,y,z), normalised on use */
+  const float* opacity_logits;  /* [N]  opacity = sigmoid(.) */
+  const float* colors;          /* [N,3] used as given */
+} pgs_explicit_ptrs;
+
+typedef struct pgs_anchor_ptrs {     /* N anchors (Sec. 3.2), caller-owned */
+  const float* x;               /* [N,3] voxel position x_v */
+  const int32_t* level;         /* [N]   LoD level k */
+  const float* log_l;           /* [N,3] log of the scaling factor l_v */
+  const float* offsets;         /* [N,10,3] learnable offsets O_v */
+  const float* feat;            /* [N,32] embedding F_v, 16-byte aligned */
+} pgs_anchor_ptrs;
+
+typedef struct pgs_mlp_ptrs {        /* shared decoder F_de (Eq. 4): 35 -> 32 (ReLU) -> 110 */
+  const float* W1;              /* [32, in_dim] row-major (out x in) */
+  const float* b1;              /* [32] */
+  const float* W2;              /* [110, 32] */
+  const float* b2;              /* [110] */
+} pgs_mlp_ptrs;
+
+typedef struct pgs_image_ptrs {      /* per-pixel outputs of pgs_render_batch (arena layout) */
+  float* rgb;                   /* [3 x pix] Eq. 5 */
+  float* depth;                 /* [pix] unbiased depth D_hat, Eq. 7 (0 where guarded) */
+  float* normal;                /* [3 x pix] un-normalised N_hat, Eq. 6, camera frame */
+  float* dist;                  /* [pix] blended plane distance D, Eq. 7 */
+  float* t_final;               /* [pix] final transmittance */
+  uint32_t* last;               /* [pix] 1 + sorted-list index of the last contributor (0: none) */
+  uint32_t* n_contrib;          /* [pix] number of contributing Gaussians (may be NULL) */
+  uint32_t* n_eval;             /* [pix] pairs evaluated before the pixel stopped (may be NULL) */
+} pgs_image_ptrs;
+
+typedef struct pgs_image_grad_ptrs { /* dL/d outputs (arena layout) */
+  float* rgb;                   /* [3 x pix] */
+  float* depth;                 /* [pix] w.r.t. D_hat */
+  float* normal;                /* [3 x pix] w.r.t. N_hat */
+} pgs_image_grad_ptrs;
+
+typedef struct pgs_target_ptrs {
+  const float* rgb;             /* [3 x pix] target colour */
+  const float* prior;           /* [pix] depth prior */
+  const float* mask;            /* [pix] 1 where the prior is trusted, else 0 */
+} pgs_target_ptrs;
+
+typedef struct pgs_loss_params {
+  float lambda_depth;           /* 1.0 */
+  float lambda_normal;          /* 0.1 */
+} pgs_loss_params;
+
+typedef struct pgs_param_grad_ptrs { /* accumulated (+=); NULL entries are skipped */
+  /* explicit mode */
+  float* means; float* log_scales; float* quats; float* opacity_logits; float* colors;
+  /* anchor mode */
+  float* x; float* log_l; float* offsets; float* feat;
+  float* W1; float* b1; float* W2; float* b2;
+} pgs_param_grad_ptrs;
+
+typedef struct pgs_stats {           /* counts of the last pgs_render_batch */
+  int64_t rows;                 /* visible (view, anchor) rows (anchor mode) */
+  int64_t gaussian_views;       /* Gaussian-view slots projected */
+  int64_t launches;             /* kernels this scene has enqueued since create (memsets excluded) */
+  int64_t pairs;                /* (Gaussian-view, tile) pairs P */
+  int64_t tiles;                /* tiles of the batch */
+  int64_t pixels;
+  uint32_t flags;               /* device error flags (bit i = status code i) */
+} pgs_stats;
+
+typedef struct pgs_scene pgs_scene;
+
+const char* pgs_last_error(void);
+const char* pgs_status_string(pgs_status s);
+void pgs_default_params(pgs_render_params* p);
+
+/* Validate the descriptor, allocate the workspace sized by its capacities.
+ * Errors: PGS_ERR_INVALID_ARG (out of range field), PGS_ERR_CUDA (allocation). */
+pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out);
+void pgs_scene_destroy(pgs_scene* s);
+
+/* Bind caller-owned parameter buffers (device pointers kept until rebound):
+ * explicit 3D Gaussians, or the anchors of Sec. 3.2 and the decoder F_de. */
+pgs_status pgs_scene_bind_explicit(pgs_scene* s, const pgs_explicit_ptrs* p);
+pgs_status pgs_scene_bind_anchors(pgs_scene* s, const pgs_anchor_ptrs* a, const pgs_mlp_ptrs* w);
+
+/* Decoder only (Eq. 4): for each view, every LoD-active anchor whose bound
+ * meets the frustum is decoded into 10 Gaussians.  Writes row r = (view,
+ * anchor) packed as view << 27 | anchor into d_rows[r] and, for Gaussian
+ * j of row r (index 10 r + j): d_mu [.,3], d_opacity [.], d_color [.,3],
+ * d_scale [.,3], d_quat [.,4] (unit).  *d_n_rows (device int64) receives the
+ * row count; rows beyond capacity_rows are dropped and flag PGS_ERR_CAPACITY.
+ * Output buffers hold capacity_rows rows (x 10 Gaussians). */
+pgs_status pgs_decode_anchors(pgs_scene* s, const pgs_camera* cams, int n_views, uint32_t* d_rows,
+                              float* d_mu, float* d_opacity, float* d_color, float* d_scale, float* d_quat,
+                              int64_t* d_n_rows, cudaStream_t stream);
+
+/* Forward of the whole batch: cull + decode + project, bin and sort by
+ * (view tile, FP32 depth, index), blend (Eq. 5-7).  The sorted lists and
+ * per-Gaussian records stay in the workspace for pgs_backward.
+ * rgb, depth, normal, dist, t_final and last are required. */
+pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* out,
+                            cudaStream_t stream);
+
+/* Loss of the rendered batch and dL/d(rgb, depth, normal) (Eq. 8-9 and the
+ * consistency term; 1/B batch mean).  d_loss[4] receives (total, rgb,
+ * depth, normal); the image gradients are OVERWRITTEN (not accumulated). */
+pgs_status pgs_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                         const pgs_target_ptrs* tgt, const pgs_loss_params* lp, float* d_loss,
+                         const pgs_image_grad_ptrs* grad, cudaStream_t stream);
+
+/* Reverse-order backward of the last pgs_render_batch (Eq. 5-7 walked back
+ * to front, then the projection and Eq. 4): transmittance is recomputed from
+ * t_final and last (no per-pair state is stored).  The cameras must equal
+ * those of that render.  Parameter gradients are accumulated. */
+pgs_status pgs_backward(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                        const pgs_image_grad_ptrs* grad, const pgs_param_grad_ptrs* pg, cudaStream_t stream);
+
+/* Synchronise the stream, return the first device-raised error and clear it. */
+pgs_status pgs_read_status(pgs_scene* s, cudaStream_t stream);
+/* Synchronise the stream and report the counts of the last render. */
+pgs_status pgs_get_stats(pgs_scene* s, pgs_stats* out, cudaStream_t stream);
+
+/* Per-stage timing (profiling aid, no counterpart in the paper).  With
+ * profiling on, every stage of the following calls is bracketed by CUDA
+ * events on the launching stream (recorded as external event nodes when the
+ * stream is being captured into a graph).  pgs_get_stage_times waits for
+ * those events and writes the most recent duration of each stage in ms (-1
+ * if it did not run) for the first n of PGS_N_STAGES stages. */
+enum pgs_stage {
+  PGS_STAGE_PROJECT = 0,      /* cull + decode + projection + tile counts */
+  PGS_STAGE_DEPTH_SORT = 1,   /* radix sort of the Gaussian-views by depth */
+  PGS_STAGE_BIN = 2,          /* offsets scan + (tile, Gaussian) pair emission */
+  PGS_STAGE_TILE_SORT = 3,    /* stable radix sort of the pairs by tile + tile ranges */
+  PGS_STAGE_BLEND_FWD = 4,
+  PGS_STAGE_LOSS = 5,
+  PGS_STAGE_BLEND_BWD = 6,
+  PGS_STAGE_PROJECT_BWD = 7,  /* projection (+ decoder input/activation) backward */
+  PGS_STAGE_WGRAD = 8,        /* decoder weight-gradient reduction */
+  PGS_N_STAGES = 9
+};
+pgs_status pgs_set_profiling(pgs_scene* s, int enable);
+pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);
+
+/* Workspace buffers of the last render, for tests and tools (device
+ * pointers owned by the scene, valid until the next render or destroy):
+ * which = 0 records float[G][16], 1 tile counts uint32[G], 2 sorted pair
+ * tiles uint32[P], 3 sorted pair Gaussian ids uint32[P], 4 tile ranges
+ * uint32[T][2], 5 depth-sorted Gaussian ids uint32[G], 6 rows uint32[rows]. */
+pgs_status pgs_scene_buffer(pgs_scene* s, int which, void** d_ptr, int64_t* capacity_elems);
+
+/* Stand-alone stages of the reorder pi (Eq. 5), exposed for the integer
+ * parity tests and for reuse.
+ *
+ * Stable LSD radix sort (one histogram pass, then one pass per 8-bit digit
+ * with decoupled look-back) of n = *d_n (device int64, clamped to n_max)
+ * key/value pairs on bits [bit_lo, bit_hi) of the keys.  The sorted result
+ * ends in (d_keys, d_vals); d_keys_alt / d_vals_alt are ping-pong buffers of
+ * the same size.  Scratch must hold pgs_sort_scratch_bytes(n_max) bytes.  A
+ * look-back wait that runs out (never expected) ORs bit PGS_ERR_TIMEOUT into
+ * *d_err (device uint32, may be NULL) and the pass completes with an
+ * unspecified order. */
+size_t pgs_sort_scratch_bytes(int64_t n_max);
+pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_alt, uint32_t* d_vals_alt,
+                          const int64_t* d_n, int64_t n_max, int bit_lo, int bit_hi, void* d_scratch,
+                          size_t scratch_bytes, uint32_t* d_err, cudaStream_t stream);
+
+/* Exclusive prefix sum of n = *d_n (device) uint32 values (optionally
+ * gathered: value k = d_in[d_index[k]]); *d_total (device uint64) = sum.
+ * Scratch must hold pgs_scan_scratch_bytes() bytes. */
+size_t pgs_scan_scratch_bytes(void);
+pgs_status pgs_exclusive_scan_u32(const uint32_t* d_in, const uint32_t* d_index, uint32_t* d_out,
+                                  unsigned long long* d_total, const int64_t* d_n, void* d_scratch,
+                                  size_t scratch_bytes, cudaStream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PGS_H_ */

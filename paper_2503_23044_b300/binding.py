@@ -1,0 +1,424 @@
+"""ctypes binding of libpgs (include/pgs.h) with torch tensors as device memory.
+
+Argument marshalling only: every step of the training step runs in the CUDA
+library.  If ``libpgs.so`` is missing the first call fails loudly; there is
+no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+from typing import Dict, List, Optional, Sequence
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpgs.so")
+
+PGS_OK, PGS_ERR_INVALID_ARG, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE, PGS_ERR_CUDA, PGS_ERR_UNSUPPORTED = range(7)
+MODE_EXPLICIT, MODE_ANCHOR = 0, 1
+DECODE_FP32, DECODE_BF16 = 0, 1
+MAX_VIEWS = 32
+
+
+class PGSError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pgs status {status}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is missing: build it with "
+                               "`python -m paper_2503_23044_b300.build` (no CPU fallback exists)")
+        _lib = C.CDLL(LIB_PATH)
+        _declare(_lib)
+    return _lib
+
+
+# ------------------------------------------------------------------ structs (mirror include/pgs.h)
+class Camera(C.Structure):
+    _fields_ = [("R", C.c_float * 9), ("t", C.c_float * 3), ("fx", C.c_float), ("fy", C.c_float),
+                ("cx", C.c_float), ("cy", C.c_float), ("width", C.c_int32), ("height", C.c_int32)]
+
+
+class RenderParams(C.Structure):
+    _fields_ = [("near_plane", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float),
+                ("alpha_max", C.c_float), ("t_min", C.c_float), ("jclamp", C.c_float), ("tile_pad", C.c_float),
+                ("lod_d0", C.c_float), ("n_levels", C.c_int32), ("bg", C.c_float), ("tile_w", C.c_int32),
+                ("tile_h", C.c_int32), ("decode_precision", C.c_int32), ("in_dim", C.c_int32)]
+
+
+class SceneDesc(C.Structure):
+    _fields_ = [("mode", C.c_int32), ("n_primitives", C.c_int64), ("max_views", C.c_int32),
+                ("max_pixels", C.c_int64), ("capacity_rows", C.c_int64), ("capacity_pairs", C.c_int64),
+                ("params", RenderParams)]
+
+
+class ExplicitPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("means", "log_scales", "quats", "opacity_logits", "colors")]
+
+
+class AnchorPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("x", "level", "log_l", "offsets", "feat")]
+
+
+class MlpPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("W1", "b1", "W2", "b2")]
+
+
+class ImagePtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal", "dist", "t_final", "last", "n_contrib", "n_eval")]
+
+
+class ImageGradPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "depth", "normal")]
+
+
+class TargetPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in ("rgb", "prior", "mask")]
+
+
+class LossParams(C.Structure):
+    _fields_ = [("lambda_depth", C.c_float), ("lambda_normal", C.c_float)]
+
+
+PARAM_GRAD_FIELDS = ("means", "log_scales", "quats", "opacity_logits", "colors",
+                     "x", "log_l", "offsets", "feat", "W1", "b1", "W2", "b2")
+
+
+class ParamGradPtrs(C.Structure):
+    _fields_ = [(n, C.c_void_p) for n in PARAM_GRAD_FIELDS]
+
+
+class Stats(C.Structure):
+    _fields_ = [("rows", C.c_int64), ("gaussian_views", C.c_int64), ("launches", C.c_int64), ("pairs", C.c_int64),
+                ("tiles", C.c_int64), ("pixels", C.c_int64), ("flags", C.c_uint32)]
+
+
+ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pgs_scene_create", "pgs_scene_destroy",
+                "pgs_scene_bind_explicit", "pgs_scene_bind_anchors", "pgs_decode_anchors", "pgs_render_batch",
+                "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
+                "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
+                "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32")
+STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad")
+
+
+def _declare(L: C.CDLL) -> None:
+    vp, i32, i64, P = C.c_void_p, C.c_int, C.c_int64, C.POINTER
+    for name in ENTRY_POINTS:
+        getattr(L, name).restype = C.c_int
+    L.pgs_last_error.restype = C.c_char_p
+    L.pgs_last_error.argtypes = []
+    L.pgs_status_string.restype = C.c_char_p
+    L.pgs_status_string.argtypes = [i32]
+    L.pgs_default_params.argtypes = [P(RenderParams)]
+    L.pgs_default_params.restype = None
+    L.pgs_scene_create.argtypes = [P(SceneDesc), P(vp)]
+    L.pgs_scene_destroy.argtypes = [vp]
+    L.pgs_scene_destroy.restype = None
+    L.pgs_scene_bind_explicit.argtypes = [vp, P(ExplicitPtrs)]
+    L.pgs_scene_bind_anchors.argtypes = [vp, P(AnchorPtrs), P(MlpPtrs)]
+    L.pgs_decode_anchors.argtypes = [vp, P(Camera), i32, vp, vp, vp, vp, vp, vp, vp, vp]
+    L.pgs_render_batch.argtypes = [vp, P(Camera), i32, P(ImagePtrs), vp]
+    L.pgs_loss_grad.argtypes = [vp, P(Camera), i32, P(ImagePtrs), P(TargetPtrs), P(LossParams), vp,
+                                P(ImageGradPtrs), vp]
+    L.pgs_backward.argtypes = [vp, P(Camera), i32, P(ImagePtrs), P(ImageGradPtrs), P(ParamGradPtrs), vp]
+    L.pgs_read_status.argtypes = [vp, vp]
+    L.pgs_get_stats.argtypes = [vp, P(Stats), vp]
+    L.pgs_set_profiling.argtypes = [vp, i32]
+    L.pgs_get_stage_times.argtypes = [vp, P(C.c_float), i32]
+    L.pgs_scene_buffer.argtypes = [vp, i32, P(vp), P(i64)]
+    L.pgs_sort_scratch_bytes.argtypes = [i64]
+    L.pgs_sort_scratch_bytes.restype = C.c_size_t
+    L.pgs_sort_pairs.argtypes = [vp, vp, vp, vp, vp, i64, i32, i32, vp, C.c_size_t, vp, vp]
+    L.pgs_scan_scratch_bytes.argtypes = []
+    L.pgs_scan_scratch_bytes.restype = C.c_size_t
+    L.pgs_exclusive_scan_u32.argtypes = [vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+
+
+def check(status: int) -> None:
+    if status != PGS_OK:
+        raise PGSError(status, lib().pgs_last_error().decode())
+
+
+def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream: Optional[torch.cuda.Stream]) -> int:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def default_params(**kw) -> RenderParams:
+    p = RenderParams()
+    lib().pgs_default_params(C.byref(p))
+    for k, v in kw.items():
+        setattr(p, k, v)
+    return p
+
+
+def pack_cameras(cams) -> C.Array:
+    """synth.Camera (or anything with R, t, fx, fy, cx, cy, width, height) -> pgs_camera[]."""
+    arr = (Camera * len(cams))()
+    for i, c in enumerate(cams):
+        arr[i].R[:] = [float(v) for v in list(c.R.reshape(-1))]
+        arr[i].t[:] = [float(v) for v in list(c.t.reshape(-1))]
+        arr[i].fx, arr[i].fy, arr[i].cx, arr[i].cy = float(c.fx), float(c.fy), float(c.cx), float(c.cy)
+        arr[i].width, arr[i].height = int(c.width), int(c.height)
+    return arr
+
+
+class _DevView:
+    """__cuda_array_interface__ over a library-owned device buffer (read-only use)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = dict(shape=(n,), typestr=typestr, data=(ptr, False), version=3)
+
+
+# ------------------------------------------------------------------ images in the ragged arena
+def arena_offsets(cams) -> List[int]:
+    off, acc = [], 0
+    for c in cams:
+        off.append(acc)
+        acc += int(c.width) * int(c.height)
+    return off + [acc]
+
+
+@dataclasses.dataclass
+class Images:
+    rgb: torch.Tensor
+    depth: torch.Tensor
+    normal: torch.Tensor
+    dist: torch.Tensor
+    t_final: torch.Tensor
+    last: torch.Tensor
+    n_contrib: torch.Tensor
+    n_eval: torch.Tensor
+    offsets: List[int]
+    shapes: List[tuple]
+
+    @staticmethod
+    def empty(cams, device="cuda") -> "Images":
+        off = arena_offsets(cams)
+        n = off[-1]
+        f = lambda k: torch.zeros(k, device=device, dtype=torch.float32)
+        i = lambda k: torch.zeros(k, device=device, dtype=torch.int32)
+        return Images(f(3 * n), f(n), f(3 * n), f(n), f(n), i(n), i(n), i(n), off,
+                      [(int(c.height), int(c.width)) for c in cams])
+
+    def ptrs(self) -> ImagePtrs:
+        return ImagePtrs(_ptr(self.rgb), _ptr(self.depth), _ptr(self.normal), _ptr(self.dist), _ptr(self.t_final),
+                         _ptr(self.last), _ptr(self.n_contrib), _ptr(self.n_eval))
+
+    def view(self, v: int) -> Dict[str, torch.Tensor]:
+        H, W = self.shapes[v]
+        a, b = self.offsets[v], self.offsets[v + 1]
+        out = dict(rgb=self.rgb[3 * a:3 * b].view(3, H, W), normal=self.normal[3 * a:3 * b].view(3, H, W))
+        for k in ("depth", "dist", "t_final", "last", "n_contrib", "n_eval"):
+            out[k] = getattr(self, k)[a:b].view(H, W)
+        return out
+
+
+@dataclasses.dataclass
+class ImageGrads:
+    rgb: torch.Tensor
+    depth: torch.Tensor
+    normal: torch.Tensor
+
+    @staticmethod
+    def empty(n_pix: int, device="cuda") -> "ImageGrads":
+        return ImageGrads(torch.zeros(3 * n_pix, device=device), torch.zeros(n_pix, device=device),
+                          torch.zeros(3 * n_pix, device=device))
+
+    @staticmethod
+    def from_views(views: Sequence[dict], device="cuda") -> "ImageGrads":
+        cat = lambda k: torch.cat([v[k].reshape(-1) for v in views]).to(device, torch.float32).contiguous()
+        return ImageGrads(cat("rgb"), cat("depth"), cat("normal"))
+
+    def ptrs(self) -> ImageGradPtrs:
+        return ImageGradPtrs(_ptr(self.rgb), _ptr(self.depth), _ptr(self.normal))
+
+
+@dataclasses.dataclass
+class Targets:
+    rgb: torch.Tensor
+    prior: torch.Tensor
+    mask: torch.Tensor
+
+    @staticmethod
+    def from_views(views: Sequence[dict], device="cuda") -> "Targets":
+        cat = lambda k: torch.cat([v[k].reshape(-1) for v in views]).to(device, torch.float32).contiguous()
+        return Targets(cat("rgb"), cat("prior"), cat("mask"))
+
+    def ptrs(self) -> TargetPtrs:
+        return TargetPtrs(_ptr(self.rgb), _ptr(self.prior), _ptr(self.mask))
+
+
+# ------------------------------------------------------------------ scene
+class Scene:
+    """Owns a pgs_scene (workspace) and keeps references to the bound tensors."""
+
+    def __init__(self, mode: int, n_primitives: int, max_views: int, max_pixels: int, capacity_pairs: int,
+                 capacity_rows: int = 0, params: Optional[RenderParams] = None):
+        self.desc = SceneDesc(mode=mode, n_primitives=n_primitives, max_views=max_views, max_pixels=max_pixels,
+                              capacity_rows=capacity_rows, capacity_pairs=capacity_pairs,
+                              params=params if params is not None else default_params())
+        h = C.c_void_p()
+        check(lib().pgs_scene_create(C.byref(self.desc), C.byref(h)))
+        self.handle = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().pgs_scene_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def bind_explicit(self, means, log_scales, quats, opacity_logits, colors):
+        ts = [t.contiguous() for t in (means, log_scales, quats, opacity_logits, colors)]
+        self._keep = ts
+        check(lib().pgs_scene_bind_explicit(self.handle, C.byref(ExplicitPtrs(*[_ptr(t) for t in ts]))))
+
+    def bind_anchors(self, x, level, log_l, offsets, feat, W1, b1, W2, b2):
+        ts = [t.contiguous() for t in (x, level, log_l, offsets, feat, W1, b1, W2, b2)]
+        self._keep = ts
+        check(lib().pgs_scene_bind_anchors(self.handle, C.byref(AnchorPtrs(*[_ptr(t) for t in ts[:5]])),
+                                           C.byref(MlpPtrs(*[_ptr(t) for t in ts[5:]]))))
+
+    def render(self, cams, images: Optional[Images] = None, stream=None, packed=None) -> Images:
+        images = images if images is not None else Images.empty(cams)
+        cc = packed if packed is not None else pack_cameras(cams)
+        check(lib().pgs_render_batch(self.handle, cc, len(cams), C.byref(images.ptrs()), _stream(stream)))
+        return images
+
+    def loss_grad(self, cams, images: Images, targets: Targets, lambda_depth=1.0, lambda_normal=0.1,
+                  loss: Optional[torch.Tensor] = None, grads: Optional[ImageGrads] = None, stream=None, packed=None):
+        n = images.offsets[-1]
+        loss = loss if loss is not None else torch.zeros(4, device=images.rgb.device)
+        grads = grads if grads is not None else ImageGrads.empty(n, images.rgb.device)
+        cc = packed if packed is not None else pack_cameras(cams)
+        check(lib().pgs_loss_grad(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(targets.ptrs()),
+                                  C.byref(LossParams(lambda_depth, lambda_normal)), _ptr(loss), C.byref(grads.ptrs()),
+                                  _stream(stream)))
+        return loss, grads
+
+    def backward(self, cams, images: Images, grads: ImageGrads, param_grads: Dict[str, torch.Tensor], stream=None,
+                 packed=None):
+        pg = ParamGradPtrs(*[_ptr(param_grads.get(n)) for n in PARAM_GRAD_FIELDS])
+        cc = packed if packed is not None else pack_cameras(cams)
+        check(lib().pgs_backward(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(grads.ptrs()),
+                                 C.byref(pg), _stream(stream)))
+
+    def decode(self, cams, capacity_rows: int, stream=None):
+        dev = "cuda"
+        G = capacity_rows * 10
+        rows = torch.zeros(capacity_rows, dtype=torch.int32, device=dev)
+        out = dict(mu=torch.zeros(G, 3, device=dev), opacity=torch.zeros(G, device=dev),
+                   color=torch.zeros(G, 3, device=dev), scale=torch.zeros(G, 3, device=dev),
+                   quat=torch.zeros(G, 4, device=dev))
+        n = torch.zeros(1, dtype=torch.int64, device=dev)
+        check(lib().pgs_decode_anchors(self.handle, pack_cameras(cams), len(cams), _ptr(rows), _ptr(out["mu"]),
+                                       _ptr(out["opacity"]), _ptr(out["color"]), _ptr(out["scale"]),
+                                       _ptr(out["quat"]), _ptr(n), _stream(stream)))
+        nr = int(n.item())
+        out = {k: v[:nr * 10] for k, v in out.items()}
+        out["rows"] = rows[:nr]
+        return out
+
+    def read_status(self, stream=None) -> None:
+        check(lib().pgs_read_status(self.handle, _stream(stream)))
+
+    def stats(self, stream=None) -> Stats:
+        st = Stats()
+        check(lib().pgs_get_stats(self.handle, C.byref(st), _stream(stream)))
+        return st
+
+    def set_profiling(self, on: bool) -> None:
+        check(lib().pgs_set_profiling(self.handle, 1 if on else 0))
+
+    def stage_times(self) -> Dict[str, float]:
+        ms = (C.c_float * len(STAGES))()
+        check(lib().pgs_get_stage_times(self.handle, ms, len(STAGES)))
+        return {k: float(v) for k, v in zip(STAGES, ms)}
+
+    def buffer(self, which: int, n: int, typestr: str = "<i4") -> torch.Tensor:
+        """Copy of the first n elements of a workspace buffer (see pgs_scene_buffer)."""
+        p, cap = C.c_void_p(), C.c_int64()
+        check(lib().pgs_scene_buffer(self.handle, which, C.byref(p), C.byref(cap)))
+        n = max(0, min(n, cap.value))
+        if n == 0:
+            return torch.zeros(0, dtype=torch.int32 if typestr == "<i4" else torch.float32, device="cuda")
+        return torch.as_tensor(_DevView(p.value, n, typestr), device="cuda").clone()
+
+
+# ------------------------------------------------------------------ stand-alone stages
+def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: int = 32):
+    """Stable radix sort of int32-stored uint32 keys/values on device (in place)."""
+    n = keys.numel()
+    if n == 0:                       # one-element buffers; the library sees n = 0
+        keys = torch.zeros(1, dtype=keys.dtype, device=keys.device)
+        vals = torch.zeros(1, dtype=vals.dtype, device=vals.device)
+    alt_k, alt_v = torch.empty_like(keys), torch.empty_like(vals)
+    nbytes = lib().pgs_sort_scratch_bytes(max(n, 1))
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=keys.device)
+    d_n = torch.tensor([n], dtype=torch.int64, device=keys.device)
+    err = torch.zeros(1, dtype=torch.int32, device=keys.device)
+    check(lib().pgs_sort_pairs(_ptr(keys), _ptr(vals), _ptr(alt_k), _ptr(alt_v), _ptr(d_n), max(n, 1), bit_lo, bit_hi,
+                               _ptr(scratch), nbytes, _ptr(err), _stream(None)))
+    return keys[:n], vals[:n], err
+
+
+def exclusive_scan(x: torch.Tensor, index: Optional[torch.Tensor] = None):
+    n = x.numel() if index is None else index.numel()
+    if x.numel() == 0:
+        x = torch.zeros(1, dtype=x.dtype, device=x.device)
+    out = torch.empty(max(n, 1), dtype=torch.int32, device=x.device)
+    total = torch.zeros(1, dtype=torch.int64, device=x.device)
+    nbytes = lib().pgs_scan_scratch_bytes()
+    scratch = torch.empty(nbytes, dtype=torch.uint8, device=x.device)
+    d_n = torch.tensor([n], dtype=torch.int64, device=x.device)
+    check(lib().pgs_exclusive_scan_u32(_ptr(x), _ptr(index), _ptr(out), _ptr(total), _ptr(d_n), _ptr(scratch), nbytes,
+                                       _stream(None)))
+    return out[:n], total
+
+
+# ------------------------------------------------------------------ autograd
+class RenderFunction(torch.autograd.Function):
+    """forward = cull + decode + project + bin/sort + blend (pgs_render_batch);
+    backward = pgs_backward (transmittance recomputed from t_final and last).
+    The scene must already be bound to ``params`` (same tensors)."""
+
+    @staticmethod
+    def forward(ctx, scene: Scene, cams, names: tuple, *params):
+        images = scene.render(cams)
+        ctx.scene, ctx.cams, ctx.names, ctx.images = scene, cams, names, images
+        ctx.shapes = [p.shape for p in params]
+        return images.rgb, images.depth, images.normal
+
+    @staticmethod
+    def backward(ctx, g_rgb, g_depth, g_normal):
+        imgs = ctx.images
+        grads = ImageGrads(*(g.contiguous() if g is not None else torch.zeros_like(t)
+                             for g, t in zip((g_rgb, g_depth, g_normal), (imgs.rgb, imgs.depth, imgs.normal))))
+        pg = {n: torch.zeros(s, device=imgs.rgb.device) for n, s in zip(ctx.names, ctx.shapes) if n != "level"}
+        ctx.scene.backward(ctx.cams, imgs, grads, pg)
+        return (None, None, None) + tuple(pg.get(n) for n in ctx.names)

@@ -1,0 +1,386 @@
+// Binning and ordering: the reorder pi of Eq. 5 as a stable sort of
+// (Gaussian-view, tile) pairs by (view tile, view depth, Gaussian index).
+//
+// Done as one LSD radix sort split in two stages: the depth digits are sorted
+// first on the G Gaussian-views (each appears once), then every Gaussian's
+// tiles are emitted in depth order and the pairs are stably sorted by tile id
+// only.  Both stages use the same onesweep pass (global digit histogram once,
+// then one pass per 8-bit digit with a decoupled look-back across tiles of
+// 4096 keys).  Every spin in the look-back is bounded: past the limit the pass
+// raises PGS_ERR_TIMEOUT and carries on, so no launch can hang.
+#include "pgs_internal.cuh"
+#include "pgs_kernels.cuh"
+
+namespace pgs {
+
+// ------------------------------------------------------------------ scan
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanChunk = kScanThreads * kScanItems;
+
+__device__ __forceinline__ unsigned long long block_exclusive_scan_u64(unsigned long long x,
+                                                                       unsigned long long* s_w,
+                                                                       unsigned long long& total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  unsigned long long inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned long long y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) s_w[warp] = inc;
+  __syncthreads();
+  if (warp == 0) {
+    unsigned long long w = lane < nw ? s_w[lane] : 0ull;
+    unsigned long long wi = w;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      unsigned long long y = __shfl_up_sync(0xffffffffu, wi, o);
+      if (lane >= o) wi += y;
+    }
+    if (lane < nw) s_w[lane] = wi - w;
+    if (lane == nw - 1) s_w[32] = wi;
+  }
+  __syncthreads();
+  unsigned long long r = s_w[warp] + inc - x;
+  total = s_w[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ void scan_range(long long n, long long& start, long long& end) {
+  const long long per = ((n + gridDim.x - 1) / gridDim.x + kScanChunk - 1) / kScanChunk * kScanChunk;
+  start = min(n, (long long)blockIdx.x * per);
+  end = min(n, start + per);
+}
+
+__device__ __forceinline__ uint32_t scan_in(const uint32_t* in, const uint32_t* index, long long k) {
+  return index ? in[index[k]] : in[k];
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const uint32_t* __restrict__ in,
+                                                              const uint32_t* __restrict__ index,
+                                                              const long long* __restrict__ d_n,
+                                                              unsigned long long* __restrict__ sums) {
+  __shared__ unsigned long long s_w[33];
+  long long s, e;
+  scan_range(*d_n, s, e);
+  unsigned long long acc = 0;
+  for (long long k = s + threadIdx.x; k < e; k += blockDim.x) acc += scan_in(in, index, k);
+  unsigned long long tot;
+  block_exclusive_scan_u64(acc, s_w, tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_spine(unsigned long long* __restrict__ sums, int nb,
+                                                     unsigned long long* __restrict__ total) {
+  __shared__ unsigned long long s_w[33];
+  unsigned long long x = threadIdx.x < nb ? sums[threadIdx.x] : 0ull;
+  unsigned long long tot;
+  unsigned long long ex = block_exclusive_scan_u64(x, s_w, tot);
+  if (threadIdx.x < nb) sums[threadIdx.x] = ex;
+  if (threadIdx.x == 0) *total = tot;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const uint32_t* __restrict__ in,
+                                                            const uint32_t* __restrict__ index,
+                                                            uint32_t* __restrict__ out,
+                                                            const long long* __restrict__ d_n,
+                                                            const unsigned long long* __restrict__ sums) {
+  __shared__ unsigned long long s_w[33];
+  long long s, e;
+  scan_range(*d_n, s, e);
+  unsigned long long carry = sums[blockIdx.x];
+  for (long long c = s; c < e; c += kScanChunk) {
+    uint32_t v[kScanItems];
+    unsigned long long loc = 0;
+    const long long b0 = c + (long long)threadIdx.x * kScanItems;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const long long k = b0 + i;
+      v[i] = k < e ? scan_in(in, index, k) : 0u;
+      loc += v[i];
+    }
+    unsigned long long tot;
+    unsigned long long ex = block_exclusive_scan_u64(loc, s_w, tot) + carry;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+      const long long k = b0 + i;
+      if (k < e) out[k] = (uint32_t)ex;
+      ex += v[i];
+    }
+    carry += tot;
+  }
+}
+
+void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
+                           const long long* d_n, unsigned long long* sums, cudaStream_t st) {
+  k_scan_reduce<<<kScanBlocks, kScanThreads, 0, st>>>(in, index, d_n, sums);
+  k_scan_spine<<<1, 1024, 0, st>>>(sums, kScanBlocks, total);
+  k_scan_down<<<kScanBlocks, kScanThreads, 0, st>>>(in, index, out, d_n, sums);
+}
+
+// ------------------------------------------------------------------ onesweep radix sort
+constexpr int kSortThreads = 256;
+constexpr int kSortWarps = kSortThreads / 32;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
+constexpr int kRadix = 256;
+constexpr uint32_t kStFlagAgg = 1u << 30, kStFlagInc = 2u << 30, kStMask = (1u << 30) - 1;
+
+__device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
+  asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// the last digit of a bit range that is not a multiple of 8 is narrower
+__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int bit_hi) {
+  const int w = bit_hi - shift < 8 ? bit_hi - shift : 8;
+  return (1u << w) - 1u;
+}
+
+SortScratch sort_scratch_layout(void* base, long long n_max) {
+  SortScratch s;
+  char* p = static_cast<char*>(base);
+  s.hist = reinterpret_cast<uint32_t*>(p);                 // [4][256]
+  s.counters = s.hist + 4 * kRadix;                         // [4]
+  s.err = s.counters + 4;                                   // [1] (+3 pad)
+  s.max_tiles = (n_max + kSortTile - 1) / kSortTile + 1;
+  s.status = s.err + 4;                                     // [2][max_tiles][256]
+  s.bytes = (size_t)(4 * kRadix + 8) * 4 + (size_t)2 * s.max_tiles * kRadix * 4;
+  return s;
+}
+
+__global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const long long* __restrict__ d_n,
+                                                   long long n_max, int bit_lo, int bit_hi, int n_pass,
+                                                   uint32_t* __restrict__ hist, uint32_t* __restrict__ status0) {
+  __shared__ uint32_t s_h[4][kRadix];
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+  __syncthreads();
+  const long long n = max(0ll, min(*d_n, n_max));
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    const uint32_t key = keys[k];
+    for (int p = 0; p < n_pass; ++p) {
+      const int sh = bit_lo + 8 * p;
+      atomicAdd(&s_h[p][(key >> sh) & digit_mask(sh, bit_hi)], 1u);
+    }
+  }
+  // clear the look-back status of the first pass for the live tiles
+  const long long n_tiles = (n + kSortTile - 1) / kSortTile;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_tiles * kRadix;
+       k += (long long)gridDim.x * blockDim.x)
+    status0[k] = 0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < n_pass * kRadix; i += blockDim.x) {
+    const uint32_t c = (&s_h[0][0])[i];
+    if (c) atomicAdd(hist + i, c);
+  }
+}
+
+__global__ void __launch_bounds__(kRadix) k_sort_hist_scan(uint32_t* __restrict__ hist, int n_pass) {
+  __shared__ unsigned long long s_w[33];
+  for (int p = 0; p < n_pass; ++p) {
+    unsigned long long tot;
+    const unsigned long long ex = block_exclusive_scan_u64(hist[p * kRadix + threadIdx.x], s_w, tot);
+    hist[p * kRadix + threadIdx.x] = (uint32_t)ex;
+  }
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+    const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
+    uint32_t* __restrict__ vout, const long long* __restrict__ d_n, long long n_max, int shift, uint32_t dmask,
+    const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
+    uint32_t* __restrict__ status_next, uint32_t* __restrict__ err, uint32_t spin_limit) {
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_whist[kSortWarps][kRadix];
+  __shared__ uint32_t s_excl[kRadix];
+  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ unsigned long long s_w[33];
+  __shared__ uint32_t s_tile;
+  const long long n = max(0ll, min(*d_n, n_max));
+  const long long n_tiles = (n + kSortTile - 1) / kSortTile;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const uint32_t lt_mask = (1u << lane) - 1u;
+  for (;;) {
+    if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
+    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    __syncthreads();
+    const long long tile = s_tile;
+    if (tile >= n_tiles) break;
+    const long long base = tile * kSortTile + warp * (kSortTile / kSortWarps);
+    uint32_t key[kSortItems], val[kSortItems], rank[kSortItems];
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+      const long long idx = base + i * 32 + lane;
+      const bool ok = idx < n;
+      key[i] = ok ? kin[idx] : 0xffffffffu;
+      val[i] = ok ? vin[idx] : 0u;
+    }
+    // warp-level stable ranking, item order (i, lane)
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+      const long long idx = base + i * 32 + lane;
+      const bool ok = idx < n;
+      const uint32_t dg = (key[i] >> shift) & dmask;
+      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? dg : 0x100u + lane);
+      const uint32_t before = s_whist[warp][dg];
+      __syncwarp();
+      rank[i] = before + __popc(peers & lt_mask);
+      if (ok && (peers & lt_mask) == 0) s_whist[warp][dg] = before + __popc(peers);
+      __syncwarp();
+    }
+    __syncthreads();
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int w = 0; w < kSortWarps; ++w) {
+      const uint32_t c = s_whist[w][d];
+      s_whist[w][d] = run;
+      run += c;
+    }
+    uint32_t* st = status + tile * kRadix;
+    st_relaxed(st + d, (tile == 0 ? kStFlagInc : kStFlagAgg) | run);
+    unsigned long long tot;
+    const uint32_t excl = (uint32_t)block_exclusive_scan_u64(run, s_w, tot);
+    s_excl[d] = excl;
+    // decoupled look-back over earlier tiles, bounded
+    uint32_t prefix = 0;
+    if (tile > 0) {
+      long long j = tile - 1;
+      uint32_t spins = 0;
+      while (j >= 0) {
+        const uint32_t w = ld_relaxed(status + j * kRadix + d);
+        const uint32_t f = w & ~kStMask;
+        if (f == 0u) {
+          if (++spins > spin_limit) { atomicOr(err, kFlagTimeout); break; }
+          if ((spins & 255u) == 0u && (ld_relaxed(err) & kFlagTimeout)) break;
+          __nanosleep(32);
+          continue;
+        }
+        prefix += w & kStMask;
+        if (f == kStFlagInc) break;
+        --j;
+      }
+      st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
+    }
+    s_gbase[d] = digit_off[d] + prefix - excl;
+    if (status_next) status_next[tile * kRadix + d] = 0u;
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+      const long long idx = base + i * 32 + lane;
+      if (idx < n) {
+        const uint32_t dg = (key[i] >> shift) & dmask;
+        const uint32_t lp = s_excl[dg] + s_whist[warp][dg] + rank[i];
+        s_keys[lp] = key[i];
+        s_vals[lp] = val[i];
+      }
+    }
+    __syncthreads();
+    const int cnt = (int)min((long long)kSortTile, n - tile * kSortTile);
+    for (int j = threadIdx.x; j < cnt; j += kSortThreads) {
+      const uint32_t k = s_keys[j];
+      const uint32_t pos = s_gbase[(k >> shift) & dmask] + (uint32_t)j;
+      if ((long long)pos < n) {   // always true unless a look-back wait ran out
+        kout[pos] = k;
+        vout[pos] = s_vals[j];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void k_copy_pairs(const uint32_t* __restrict__ ks, const uint32_t* __restrict__ vs, uint32_t* __restrict__ kd,
+                             uint32_t* __restrict__ vd, const long long* __restrict__ d_n, long long n_max) {
+  const long long n = max(0ll, min(*d_n, n_max));
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+    kd[k] = ks[k];
+    vd[k] = vs[k];
+  }
+}
+
+int sort_passes(int bit_lo, int bit_hi) { return (bit_hi - bit_lo + 7) / 8; }
+
+cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                              const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
+                              uint32_t* err, uint32_t spin_limit, int num_sms, cudaStream_t st, int* n_launch) {
+  const int np = sort_passes(bit_lo, bit_hi);
+  if (n_launch) *n_launch = 0;
+  if (np <= 0) return cudaSuccess;
+  if (n_launch) *n_launch = 2 + np + (np & 1);
+  cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)(4 * kRadix + 4) * 4, st);
+  if (e != cudaSuccess) return e;
+  uint32_t* status[2] = {s.status, s.status + (size_t)s.max_tiles * kRadix};
+  k_sort_hist<<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0]);
+  k_sort_hist_scan<<<1, kRadix, 0, st>>>(s.hist, np);
+  uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
+  for (int p = 0; p < np; ++p) {
+    k_sort_pass<<<num_sms * 2, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + 8 * p,
+                                                     digit_mask(bit_lo + 8 * p, bit_hi), s.hist + p * kRadix,
+                                                     s.counters + p, status[p & 1],
+                                                     p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit);
+    uint32_t* t;
+    t = ki; ki = ko; ko = t;
+    t = vi; vi = vo; vo = t;
+  }
+  if (ki != keys) k_copy_pairs<<<num_sms * 4, 256, 0, st>>>(ki, vi, keys, vals, d_n, n_max);
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ pair emission and tile ranges
+__global__ void __launch_bounds__(256) k_emit_pairs(const __grid_constant__ BatchDev b, const float4* __restrict__ rec,
+                                                    const uint32_t* __restrict__ counts,
+                                                    const uint32_t* __restrict__ sorted_g,
+                                                    const uint32_t* __restrict__ offs, const long long* __restrict__ d_ng,
+                                                    long long cap, int mode, long long n_explicit,
+                                                    const uint32_t* __restrict__ rows, uint32_t* __restrict__ tiles_out,
+                                                    uint32_t* __restrict__ g_out, uint32_t* err) {
+  const long long ng = *d_ng;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ng; k += (long long)gridDim.x * blockDim.x) {
+    const uint32_t g = sorted_g[k];
+    const uint32_t cnt = counts[g];
+    if (!cnt) continue;
+    const int vi = mode == PGS_MODE_EXPLICIT ? (int)(g / n_explicit) : (int)(rows[g / kNOff] >> 27);
+    const ViewDev& v = b.v[vi];
+    TileEllipse e;
+    const float4 r0 = rec[(long long)g * kRecF4], r1 = rec[(long long)g * kRecF4 + 1];
+    if (!tile_ellipse_setup(r0, r1, b.p, e)) continue;
+    long long o = offs[k];
+    const long long o_end = o + cnt;
+    const int tb = v.tile_base, tx_n = v.tiles_x;
+    for_each_tile_row(e, v, b.p.tile_w, b.p.tile_h, [&](int ty, int c0, int c1) {
+      for (int tx = c0; tx <= c1; ++tx) {
+        if (o < o_end && o < cap) {
+          tiles_out[o] = (uint32_t)(tb + ty * tx_n + tx);
+          g_out[o] = g;
+        }
+        ++o;
+      }
+    });
+    if (o != o_end) set_flag(err, kFlagCapacity);   // count and emit disagree: never expected
+  }
+}
+
+__global__ void k_pairs_total(const unsigned long long* __restrict__ total, long long cap, long long* __restrict__ d_p,
+                              uint32_t* err) {
+  const unsigned long long t = *total;
+  if (t > (unsigned long long)cap) set_flag(err, kFlagCapacity);
+  *d_p = (long long)min(t, (unsigned long long)cap);
+}
+
+__global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const long long* __restrict__ d_p,
+                              uint2* __restrict__ ranges) {
+  const long long P = *d_p;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
+    const uint32_t t = tiles[i];
+    if (i == 0 || tiles[i - 1] != t) ranges[t].x = (uint32_t)i;
+    if (i == P - 1 || tiles[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
+  }
+}
+
+}  // namespace pgs

@@ -1,0 +1,74 @@
+// Kernel entry points and launch helpers shared between the translation units.
+#pragma once
+#include "pgs_internal.cuh"
+
+namespace pgs {
+
+constexpr int kScanBlocks = 592;   // 4 x 148 SMs
+constexpr int kLossBlocks = 1184;  // 8 x 148 SMs
+// kernels enqueued by the multi-kernel launch helpers
+constexpr int kScanLaunches = 3, kLossLaunches = 3, kWgradLaunches = 2;
+
+struct DecodeOut {
+  float *mu, *opacity, *color, *scale, *quat;
+};
+
+struct SortScratch {
+  uint32_t* hist;
+  uint32_t* counters;
+  uint32_t* err;
+  uint32_t* status;
+  long long max_tiles;
+  size_t bytes;
+};
+
+// k_project.cu
+__global__ void k_project_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N, float4* rec,
+                                   uint32_t* counts, uint32_t* keys);
+__global__ void k_anchor_cull(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, long long Na, uint32_t* flags);
+__global__ void k_compact_rows(const uint32_t* flags, const uint32_t* offs, long long total, long long Na,
+                               uint32_t* rows, long long cap, uint32_t* err);
+__global__ void k_decode_project(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, pgs_mlp_ptrs Wt,
+                                 const uint32_t* rows, const long long* n_rows_p, long long cap, float4* rec,
+                                 uint32_t* counts, uint32_t* keys, DecodeOut dec);
+
+// k_sort.cu
+void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
+                           const long long* d_n, unsigned long long* sums, cudaStream_t st);
+SortScratch sort_scratch_layout(void* base, long long n_max);
+int sort_passes(int bit_lo, int bit_hi);
+cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                              const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
+                              uint32_t* err, uint32_t spin_limit, int num_sms, cudaStream_t st,
+                              int* n_launch = nullptr);
+__global__ void k_emit_pairs(const __grid_constant__ BatchDev b, const float4* rec, const uint32_t* counts,
+                             const uint32_t* sorted_g, const uint32_t* offs, const long long* d_ng, long long cap,
+                             int mode, long long n_explicit, const uint32_t* rows, uint32_t* tiles_out,
+                             uint32_t* g_out, uint32_t* err);
+__global__ void k_pairs_total(const unsigned long long* total, long long cap, long long* d_p, uint32_t* err);
+__global__ void k_tile_ranges(const uint32_t* tiles, const long long* d_p, uint2* ranges);
+
+// k_blend.cu
+bool launch_blend_fwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
+                      const pgs_image_ptrs& o, cudaStream_t st);
+bool launch_blend_bwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
+                      const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, cudaStream_t st);
+
+// k_loss.cu
+void launch_loss(const BatchDev& b, const pgs_image_ptrs& img, const pgs_target_ptrs& tgt, const pgs_loss_params& lp,
+                 float* loss, const pgs_image_grad_ptrs& g, uint32_t* counts, float* partials, uint32_t* err,
+                 cudaStream_t st);
+
+// k_backward.cu
+__global__ void k_project_bwd_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N,
+                                       const float* grad, pgs_param_grad_ptrs out, uint32_t* err);
+__global__ void k_decode_bwd(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, pgs_mlp_ptrs Wt,
+                             const uint32_t* rows, const long long* n_rows_p, long long cap, const float* grad,
+                             pgs_param_grad_ptrs out, float* sc_dZ, float* sc_H, float* sc_dH, float* sc_X,
+                             uint32_t* err);
+int mlp_wgrad_outputs(int in_dim);
+void launch_mlp_wgrad(const float* dZ, const float* H, const float* dH, const float* X, const long long* n_rows,
+                      long long cap, int in_dim, float* partials, int nb, const pgs_param_grad_ptrs& out,
+                      cudaStream_t st);
+
+}  // namespace pgs
