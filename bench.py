@@ -1,0 +1,425 @@
+"""Throughput of the batch-level RGB-Depth-Normal training step on one B300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgs|reference]
+
+A step is one pass of the whole hot path over one batch: LoD/frustum cull,
+decoder, projection, depth sort, tile binning, tile sort, forward blend,
+losses, backward blend, projection/decoder backward and the decoder's weight
+gradients.  Workload: 8 aerial views of 1600x1064 over 200k anchors (2M
+neural Gaussians) on a 3-level LoD hierarchy, seeded synthetic terrain.
+
+Batched form (the headline): all views in one call sequence, captured once in
+a CUDA graph and replayed.  Plain form: one view per call sequence, eager.
+Under torchrun each rank renders its own batch (weak scaling, no collective
+on the data path).  ``--impl reference`` times the FP64 CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+import torch
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "train views/s fwd+bwd RGB-D-N, 2M Gaussians @1600x1064, batched vs plain"
+FP32_LANES_PER_SM = 128
+# FP32 op model of the blend kernels (per pixel-Gaussian evaluation): the
+# power of the Gaussian costs 12 flops (4 sub, 4 mul, 2 fma); a contributing
+# pair adds 18 in the forward (alpha, transmittance, weight, 7 fma) and ~70 in
+# the backward (transmittance undo, dL/dalpha over 7 channels, suffix sums,
+# 13 per-pair gradients).
+FWD_FLOPS_EVAL, FWD_FLOPS_CONTRIB = 12, 18
+BWD_FLOPS_EVAL, BWD_FLOPS_CONTRIB = 12, 70
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return dict(hbm_gbs=float(d["hbm_gbs"]), sm_max_mhz=float(d.get("sm_max_mhz", 2032.0)), src="measured")
+    return dict(hbm_gbs=6400.0, sm_max_mhz=2032.0, src="fallback")
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.f,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path or not os.path.exists(self.path):
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        rows = [l.strip().split(",") for l in open(self.path) if l.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                mx = float(r[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=mx, reasons=sorted(reasons),
+                    samples=len(sm))
+
+
+# ------------------------------------------------------------------ workload
+def make_workload(name: str, seed: int, device: str):
+    from paper_2503_23044_b300 import synth
+    sc = synth.anchor_scene(name, seed=seed)
+    targets = [synth.march_targets(sc["terrain"], c, stride=4, device=device, seed=seed * 100 + i)
+               for i, c in enumerate(sc["cameras"])]
+    return sc, targets
+
+
+def build_scene(sc, B, device):
+    cams = sc["cameras"]
+    Na = len(sc["x"])
+    params = B.default_params(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
+    npix = sum(c.width * c.height for c in cams)
+    scene = B.Scene(B.MODE_ANCHOR, Na, len(cams), npix, (1 << 29), capacity_rows=Na * len(cams), params=params)
+    t = {k: torch.tensor(np.asarray(sc[k]), device=device).contiguous() for k in ("x", "level", "log_l", "offsets", "feat")}
+    for k, v in sc["mlp"].items():
+        t[k] = torch.tensor(np.asarray(v, np.float32), device=device).contiguous()
+    scene.bind_anchors(t["x"], t["level"], t["log_l"], t["offsets"], t["feat"], t["W1"], t["b1"], t["W2"], t["b2"])
+    pg = {k: torch.zeros_like(v, dtype=torch.float32) for k, v in t.items() if k != "level"}
+    return scene, t, pg
+
+
+# ------------------------------------------------------------------ CPU oracle baseline
+def cpu_oracle_sample(sc, targets, view: int, crop_size: int = 64):
+    """FP64 oracle on one view: decode + project every LoD-active anchor, then a
+    crop_size^2 crop forward + backward (seeded image gradient).  Returns
+    (seconds of the whole-view setup, seconds of the crop, crop pixels)."""
+    import oracle as O
+    from paper_2503_23044_b300 import synth
+    cam = sc["cameras"][view]
+    rp = O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
+    x0, y0 = cam.width // 2 - crop_size // 2, cam.height * 2 // 3 - crop_size // 2
+    crop = (x0, y0, crop_size, crop_size)
+    g = synth.random_image_grads([cam], seed=view, scale=1e-2, crops=[crop])[0]
+    g = {k: v[..., y0:y0 + crop_size, x0:x0 + crop_size] for k, v in g.items()}
+    leaves = O.leaves_anchor(sc)
+    t0 = time.perf_counter()
+    c = O.camera(cam)
+    gs = O.gaussians_for_view(sc, leaves, c, rp)
+    proj = O.project(gs["mu"], gs["scale"], gs["quat"], gs["opacity"], gs["color"], c, rp)
+    t1 = time.perf_counter()
+    O.render_view(proj, c, rp, crop, 32, {k: O._t(v) for k, v in g.items()})
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, crop_size * crop_size
+
+
+def cpu_views_per_s(sc, targets, views, crop_size=64):
+    total_t, parts = 0.0, []
+    for v in views:
+        ts, tc, npx = cpu_oracle_sample(sc, targets, v, crop_size)
+        cam = sc["cameras"][v]
+        t_view = ts + tc * (cam.width * cam.height / npx)
+        total_t += t_view
+        parts.append((ts, tc))
+    return len(views) / total_t, parts
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    torch.set_num_threads(max(1, len(os.sched_getaffinity(0))))
+    from paper_2503_23044_b300 import synth
+    sc = synth.anchor_scene(args.workload, seed=0)
+    V = len(sc["cameras"])
+    per_step = []
+    for s in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        vps, _ = cpu_views_per_s(sc, None, [s % V])
+        per_step.append(1.0 / vps)
+        _ = t0
+    timed = per_step[args.warmup:]
+    value = len(timed) / sum(timed)
+    cores = torch.get_num_threads()
+    sample = (f"per step one of the {V} 1600x1064 views: FP64 decode+projection of every LoD-active anchor, then a "
+              "64x64 crop fwd+bwd; per-pixel cost extrapolated to the full frame")
+    line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
+                ms_per_step=1e3 * sum(timed) / len(timed), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
+                            resolution="1600x1064", l2="n/a (CPU)"),
+                cpu_baseline=dict(value=value, unit="views/s", cores=cores, kind="oracle", sample=sample),
+                e2e=dict(value=value, unit="views/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ GPU arm
+def run_pgs(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    device = f"cuda:{local}"
+    from paper_2503_23044_b300 import binding as B
+    sc, tviews = make_workload(args.workload, seed=rank, device=device)
+    cams = sc["cameras"]
+    V = len(cams)
+    packed = B.pack_cameras(cams)
+    scene, t, pg = build_scene(sc, B, device)
+    targets = B.Targets.from_views(tviews, device=device)
+    images = B.Images.empty(cams, device=device)
+    n_pix = images.offsets[-1]
+    grads = B.ImageGrads.empty(n_pix, device=device)
+    loss = torch.zeros(4, device=device)
+    stream = torch.cuda.Stream(device=device)
+
+    def step():
+        scene.render(cams, images, packed=packed)
+        scene.loss_grad(cams, images, targets, loss=loss, grads=grads, packed=packed)
+        for v in pg.values():
+            v.zero_()
+        scene.backward(cams, images, grads, pg, packed=packed)
+
+    # eager warm-up, counts and launch accounting
+    with torch.cuda.stream(stream):
+        step()
+    scene.read_status(stream)
+    st0 = scene.stats(stream)
+    with torch.cuda.stream(stream):
+        step()
+    st1 = scene.stats(stream)
+    launches_per_step = int(st1.launches - st0.launches)
+    scene.read_status(stream)
+    n_eval = float(images.n_eval.double().sum())
+    n_contrib = float(images.n_contrib.double().sum())
+
+    # capture the whole step in one CUDA graph, with the stage events inside it
+    scene.set_profiling(True)
+    graph = torch.cuda.CUDAGraph()
+    use_graph = True
+    try:
+        with torch.cuda.stream(stream):
+            stream.synchronize()
+            with torch.cuda.graph(graph, stream=stream):
+                step()
+    except Exception as e:  # pragma: no cover - reported, not hidden
+        print(f"graph capture failed ({e}); timing the eager step", file=sys.stderr)
+        use_graph = False
+    run = graph.replay if use_graph else step
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=device)   # > 126 MB L2
+    for _ in range(args.warmup):
+        with torch.cuda.stream(stream):
+            run()
+    stream.synchronize()
+    scene.read_status(stream)
+    stage_sum = {k: 0.0 for k in B.STAGES}
+    step_ms = []
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)                      # evict L2 between timed steps
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                run()
+                e1.record(stream)
+            e1.synchronize()
+            step_ms.append(e0.elapsed_time(e1))
+            for k, v in scene.stage_times().items():
+                stage_sum[k] += max(v, 0.0)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist is not None:
+        dist.barrier()
+    scene.read_status(stream)
+    tot_ms = float(sum(step_ms))
+    if dist is not None:
+        tt = torch.tensor([tot_ms], device=device)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        tot_ms = float(tt.item())
+    ms_per_step = tot_ms / args.steps
+    value = world * V * args.steps / (tot_ms / 1e3)
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+    stats = scene.stats(stream)
+    scene.set_profiling(False)
+
+    # plain form: one view per call sequence, eager, no graph
+    plain_vps = None
+    if not args.no_plain:
+        pimgs = [B.Images.empty([c], device=device) for c in cams]
+        ptg = [B.Targets.from_views([tv], device=device) for tv in tviews]
+        pgr = [B.ImageGrads.empty(c.width * c.height, device=device) for c in cams]
+        pk = [B.pack_cameras([c]) for c in cams]
+
+        def plain_step():
+            for i, c in enumerate(cams):
+                scene.render([c], pimgs[i], packed=pk[i])
+                scene.loss_grad([c], pimgs[i], ptg[i], loss=loss, grads=pgr[i], packed=pk[i])
+                scene.backward([c], pimgs[i], pgr[i], pg, packed=pk[i])
+
+        with torch.cuda.stream(stream):
+            plain_step()
+        stream.synchronize()
+        ks = max(1, min(args.steps, 5))
+        pm = 0.0
+        for _ in range(ks):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plain_step()
+                e1.record(stream)
+            e1.synchronize()
+            pm += e0.elapsed_time(e1)
+        scene.read_status(stream)
+        plain_vps = V * ks / (pm / 1e3)
+
+    # end to end through the public API: targets from pinned host memory in,
+    # loss scalars out, every step
+    host_t = [x.cpu().pin_memory() for x in (targets.rgb, targets.prior, targets.mask)]
+    host_loss = torch.zeros(4).pin_memory()
+    h2d = sum(x.numel() * x.element_size() for x in host_t)
+    d2h = host_loss.numel() * 4
+    ke = max(1, min(args.steps, 10))
+    em = 0.0
+    for _ in range(ke):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            targets.rgb.copy_(host_t[0], non_blocking=True)
+            targets.prior.copy_(host_t[1], non_blocking=True)
+            targets.mask.copy_(host_t[2], non_blocking=True)
+            run()
+            host_loss.copy_(loss, non_blocking=True)
+            e1.record(stream)
+        e1.synchronize()
+        em += e0.elapsed_time(e1)
+    e2e_vps = world * V * ke / (em / 1e3)
+
+    # roofline of the dominant kernel
+    peaks = _peaks()
+    dom = max(("blend_bwd", "blend_fwd", "tile_sort", "depth_sort", "project", "project_bwd", "wgrad", "bin", "loss"),
+              key=lambda k: stage_ms.get(k, 0.0))
+    sm_count = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    P = int(stats.pairs)
+    if dom in ("blend_bwd", "blend_fwd"):
+        fl = (BWD_FLOPS_EVAL * n_eval + BWD_FLOPS_CONTRIB * n_contrib) if dom == "blend_bwd" else \
+             (FWD_FLOPS_EVAL * n_eval + FWD_FLOPS_CONTRIB * n_contrib)
+        ach = fl / (stage_ms[dom] / 1e3) / 1e12
+        roof = dict(bound="alu", kernel=f"k_{dom}", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                    traffic=None, flops_per_launch=fl, peak_src=f"{sm_count} SMs x 128 FP32 lanes x 2 x "
+                    f"{peaks['sm_max_mhz']:.0f} MHz")
+    else:
+        nb = {"tile_sort": 2 * 16 * P * math.ceil(max(1, math.log2(max(2, stats.tiles))) / 8) + 4 * P,
+              "depth_sort": 4 * 16 * stats.gaussian_views + 4 * stats.gaussian_views}.get(dom, 64 * stats.gaussian_views)
+        ach = nb / (stage_ms[dom] / 1e3) / 1e9
+        roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                    frac=ach / peaks["hbm_gbs"], traffic=None, bytes_per_launch=nb)
+    roof["peak_source"] = peaks["src"]
+
+    # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        torch.set_num_threads(max(1, len(os.sched_getaffinity(0))))
+        vps, parts = cpu_views_per_s(sc, tviews, [0])
+        cpu = dict(value=vps, unit="views/s", cores=torch.get_num_threads(), kind="oracle",
+                   sample="view 0: FP64 decode+projection of every LoD-active anchor, then one 64x64 crop fwd+bwd; "
+                          "per-pixel cost extrapolated to 1600x1064",
+                   seconds=dict(setup=parts[0][0], crop=parts[0][1]))
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
+                    ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
+                    data="synthetic",
+                    config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
+                                resolution="1600x1064", form="batched: all views per call, CUDA graph" if use_graph
+                                else "batched: all views per call, eager", decode="FP32 SIMT",
+                                tile="16x16", l2="flushed between timed steps (256 MB write)",
+                                parallelism=f"replicas x{world}"),
+                    plain=dict(value=plain_vps, unit="views/s", form="one view per call sequence, eager"),
+                    e2e=dict(value=e2e_vps, unit="views/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
+                    gpu_launches=launches_per_step * args.steps,
+                    roofline=roof, stage_ms=stage_ms, cpu_baseline=cpu, clocks=clocks,
+                    counts=dict(rows=int(stats.rows), gaussian_views=int(stats.gaussian_views), pairs=P,
+                                tiles=int(stats.tiles), pixels=int(stats.pixels), n_eval=n_eval, n_contrib=n_contrib),
+                    wall_s=wall)
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pgs", choices=("pgs", "reference"))
+    ap.add_argument("--workload", default="batch8_1600")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3) if args.impl == "pgs" else args.warmup
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_pgs(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

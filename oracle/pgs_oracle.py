@@ -54,7 +54,7 @@ N_OFF = 10
 # decision inside it are flagged ambiguous.
 AMB_ALPHA = 5e-5
 AMB_T = 1e-4
-AMB_GAUSS = 2e-6
+AMB_GAUSS = 1e-6
 
 
 @dataclasses.dataclass
