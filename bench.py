@@ -149,7 +149,7 @@ def cpu_oracle_sample(sc, targets, view: int, crop_size: int = 64):
     gs = O.gaussians_for_view(sc, leaves, c, rp)
     proj = O.project(gs["mu"], gs["scale"], gs["quat"], gs["opacity"], gs["color"], c, rp)
     t1 = time.perf_counter()
-    O.render_view(proj, c, rp, crop, 32, {k: O._t(v) for k, v in g.items()})
+    O.render_view(proj, c, rp, crop, 32, {k: v.double() for k, v in g.items()})
     t2 = time.perf_counter()
     return t1 - t0, t2 - t1, crop_size * crop_size
 
@@ -376,11 +376,11 @@ def run_pgs(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         torch.set_num_threads(max(1, len(os.sched_getaffinity(0))))
-        vps, parts = cpu_views_per_s(sc, tviews, [0])
+        vps, parts = cpu_views_per_s(sc, tviews, list(range(V)))
         cpu = dict(value=vps, unit="views/s", cores=torch.get_num_threads(), kind="oracle",
-                   sample="view 0: FP64 decode+projection of every LoD-active anchor, then one 64x64 crop fwd+bwd; "
-                          "per-pixel cost extrapolated to 1600x1064",
-                   seconds=dict(setup=parts[0][0], crop=parts[0][1]))
+                   sample=f"all {V} views: FP64 decode+projection of every LoD-active anchor, then one 64x64 crop "
+                          "fwd+bwd per view; per-pixel cost extrapolated to 1600x1064",
+                   seconds=dict(setup=sum(p[0] for p in parts), crops=sum(p[1] for p in parts)))
 
     clocks = clk.summary()
     if rank == 0:
@@ -408,7 +408,7 @@ def run_pgs(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pgs", choices=("pgs", "reference"))
     ap.add_argument("--workload", default="batch8_1600")
