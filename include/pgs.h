@@ -277,6 +277,25 @@ pgs_status pgs_exclusive_scan_u32(const uint32_t* d_in, const uint32_t* d_index,
                                   unsigned long long* d_total, const int64_t* d_n, void* d_scratch,
                                   size_t scratch_bytes, cudaStream_t stream);
 
+/* The same radix sort for callers that cannot allocate device memory (no
+ * counterpart in the paper): code running inside an allocator or memory-pool
+ * callback, plug-ins whose host framework owns all device memory, real-time
+ * paths that must not risk an allocation failure.  Sorts n (host value,
+ * 0 <= n <= 1048576) key/value pairs in place on bits [bit_lo, bit_hi), with
+ * the same stable order as pgs_sort_pairs.  All scratch (histograms,
+ * look-back status, ping-pong keys and values) sits in one fixed array of
+ * about 8.9 MB inside the library's device image, which every GPU that loads
+ * the library holds until the process exits; nothing is allocated or freed.
+ * The first call on a device looks up that array's device address (make it
+ * before any stream capture).  Every call on a device shares the array and it
+ * keeps the last call's contents, so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them.  Larger n is rejected with
+ * PGS_ERR_INVALID_ARG and a message in pgs_last_error().  A look-back wait
+ * that runs out ORs PGS_ERR_TIMEOUT into *d_err (device uint32, not cleared
+ * by the call; may be NULL). */
+pgs_status pgs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n, int bit_lo, int bit_hi,
+                                  uint32_t* d_err, cudaStream_t stream);
+
 #ifdef __cplusplus
 }
 #endif

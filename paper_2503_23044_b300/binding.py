@@ -106,7 +106,7 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_scene_bind_explicit", "pgs_scene_bind_anchors", "pgs_decode_anchors", "pgs_render_batch",
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
-                "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32")
+                "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad")
 
 
@@ -141,6 +141,7 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_scan_scratch_bytes.argtypes = []
     L.pgs_scan_scratch_bytes.restype = C.c_size_t
     L.pgs_exclusive_scan_u32.argtypes = [vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
+    L.pgs_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
 
 
 def check(status: int) -> None:
@@ -385,6 +386,19 @@ def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: 
     check(lib().pgs_sort_pairs(_ptr(keys), _ptr(vals), _ptr(alt_k), _ptr(alt_v), _ptr(d_n), max(n, 1), bit_lo, bit_hi,
                                _ptr(scratch), nbytes, _ptr(err), _stream(None)))
     return keys[:n], vals[:n], err
+
+
+NOALLOC_MAX_N = 1 << 20
+
+
+def sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: int = 32,
+                       err: Optional[torch.Tensor] = None):
+    """In-place stable radix sort through pgs_sort_pairs_noalloc: the library
+    allocates nothing (its scratch is a fixed array in its device image), for
+    callers that must not allocate device memory.  n <= NOALLOC_MAX_N."""
+    check(lib().pgs_sort_pairs_noalloc(_ptr(keys), _ptr(vals), keys.numel(), bit_lo, bit_hi, _ptr(err),
+                                       _stream(None)))
+    return keys, vals
 
 
 def exclusive_scan(x: torch.Tensor, index: Optional[torch.Tensor] = None):

@@ -65,6 +65,10 @@ cudaError_t dmalloc(T** p, size_t n) {
 
 }  // namespace
 
+namespace pgs {
+void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+}  // namespace pgs
+
 struct pgs_scene {
   pgs_scene_desc d{};
   int device = 0, num_sms = 148;

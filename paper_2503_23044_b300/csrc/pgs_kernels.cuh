@@ -22,6 +22,9 @@ struct SortScratch {
   size_t bytes;
 };
 
+// pgs_api.cu: message returned by pgs_last_error() on this host thread
+void set_last_error(const char* msg);
+
 // k_project.cu
 __global__ void k_project_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N, float4* rec,
                                    uint32_t* counts, uint32_t* keys);
