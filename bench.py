@@ -116,12 +116,13 @@ def make_workload(name: str, seed: int, device: str):
     return sc, targets
 
 
-def build_scene(sc, B, device):
+def build_scene(sc, B, device, cap_pairs=None, cap_rows=None):
     cams = sc["cameras"]
     Na = len(sc["x"])
     params = B.default_params(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
     npix = sum(c.width * c.height for c in cams)
-    scene = B.Scene(B.MODE_ANCHOR, Na, len(cams), npix, (1 << 29), capacity_rows=Na * len(cams), params=params)
+    scene = B.Scene(B.MODE_ANCHOR, Na, len(cams), npix, cap_pairs or (1 << 29),
+                    capacity_rows=cap_rows or Na * len(cams), params=params)
     t = {k: torch.tensor(np.asarray(sc[k]), device=device).contiguous() for k in ("x", "level", "log_l", "offsets", "feat")}
     for k, v in sc["mlp"].items():
         t[k] = torch.tensor(np.asarray(v, np.float32), device=device).contiguous()
@@ -211,7 +212,7 @@ def run_pgs(args):
     cams = sc["cameras"]
     V = len(cams)
     packed = B.pack_cameras(cams)
-    scene, t, pg = build_scene(sc, B, device)
+    scene, t, pg = build_scene(sc, B, device, args.cap_pairs, args.cap_rows)
     targets = B.Targets.from_views(tviews, device=device)
     images = B.Images.empty(cams, device=device)
     n_pix = images.offsets[-1]
@@ -414,6 +415,8 @@ def main():
     ap.add_argument("--workload", default="batch8_1600")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cap-pairs", type=int, default=None, help="pair capacity (default 2^29)")
+    ap.add_argument("--cap-rows", type=int, default=None, help="visible (view, anchor) row capacity")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3) if args.impl == "pgs" else args.warmup
     if args.impl == "reference":
