@@ -93,7 +93,15 @@ __device__ __forceinline__ void fwd_write(const PixF& P, const ViewDev& v, const
 }
 
 // Each thread owns two vertically adjacent pixels of the tile, so one staged
-// record and its dx serve both, and each warp covers a compact 16 x 4 block.
+// record and its dx serve both; each warp covers a compact 8 x 8 block of the
+// tile, so its pixels tend to agree on which Gaussians they skip or take.
+template <int TW>
+__device__ __forceinline__ void warp_block_pixel(int tx, int ty, int TH, int& px, int& py0) {
+  const int w = (int)threadIdx.x >> 5, l = (int)threadIdx.x & 31;
+  constexpr int WX = TW / 8;
+  px = tx * TW + (w % WX) * 8 + (l & 7);
+  py0 = ty * TH + (w / WX) * 8 + 2 * (l >> 3);
+}
 template <int TW, int TH>
 __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant__ BatchDev b,
                                                            const float4* __restrict__ rec,
@@ -107,7 +115,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
   const int ty = lt / v.tiles_x, tx = lt - ty * v.tiles_x;
-  const int px = tx * TW + (int)threadIdx.x % TW, py0 = ty * TH + 2 * ((int)threadIdx.x / TW);
+  int px, py0;
+  warp_block_pixel<TW>(tx, ty, TH, px, py0);
   const float fx_rel = (float)px + 0.5f - v.cx;
   const uint2 rg = ranges[tile];
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max, t_min = b.p.t_min;
@@ -170,7 +179,7 @@ __device__ __forceinline__ float warp_transpose_reduce16(float v[16], int lane) 
 struct PixB {            // backward state of one pixel
   float fy, T;
   float gC0, gC1, gC2, gD, gN0, gN1, gN2;       // dL/d(colour, D, N) at the pixel
-  float S0, S1, S2, SD, SN0, SN1, SN2;          // suffix sums of the later contributors
+  float GS;     // sum over channels of g_ch * (suffix sum of the later contributors' channel values)
   uint32_t last;
 };
 
@@ -179,7 +188,7 @@ __device__ __forceinline__ void bwd_setup(PixB& P, const ViewDev& v, const Param
   P.fy = (float)py + 0.5f - v.cy;
   P.T = 1.f; P.last = 0;
   P.gC0 = P.gC1 = P.gC2 = P.gD = P.gN0 = P.gN1 = P.gN2 = 0.f;
-  P.S0 = P.S1 = P.S2 = P.SD = P.SN0 = P.SN1 = P.SN2 = 0.f;
+  P.GS = 0.f;
   if (px >= v.W || py >= v.H) return;
   const long long HW = (long long)v.W * v.H;
   const long long q = v.pix_off + (long long)py * v.W + px;
@@ -201,11 +210,15 @@ __device__ __forceinline__ void bwd_setup(PixB& P, const ViewDev& v, const Param
     const float k = -gDh * D * ind * ind;
     P.gN0 += k * rx; P.gN1 += k * ry; P.gN2 += k;
   }
-  P.S0 = P.S1 = P.S2 = P.T * p.bg;
+  // the background enters the RGB suffix sums with weight T_final
+  P.GS = P.T * p.bg * (P.gC0 + P.gC1 + P.gC2);
 }
 
-// Undo one contributor of the pixel (back to front) and add its 13 gradients
+// Undo one contributor of the pixel (back to front) and add its per-pixel sums
 // into vals; returns false if the pair did not contribute in the forward.
+//   vals[0..5]  = sum G dx, G dy, G dx^2, G dx dy, G dy^2, G   (G = dL/dalpha * alpha_raw)
+//   vals[6..12] = sum w gC (3), w gD, w gN (3)
+// dL/dalpha_i = T_i (g . f_i) - (g . S_i) / (1 - alpha_i), with g . S_i carried as one scalar.
 __device__ __forceinline__ bool bwd_pair(PixB& P, const BlendSmem& s, int k, float dx, float4 q, float a_max,
                                          float vals[16]) {
   const float dy = rel_d(P.fy, s.m[k].y, s.m[k].w);
@@ -214,36 +227,47 @@ __device__ __forceinline__ bool bwd_pair(PixB& P, const BlendSmem& s, int k, flo
   if (power > 0.f || !(power >= nn.w)) return false;
   const float a_raw = __fmul_rn(q.w, ex2_approx(power));
   const float alpha = fminf(a_max, a_raw);
-  const float om = __fsub_rn(1.f, alpha);
-  const float iom = 1.f / om;
+  const float iom = 1.f / __fsub_rn(1.f, alpha);
   P.T = P.T * iom;
   const float w = alpha * P.T;
   const float4 c = s.c[k];
-  const float dLda = P.gC0 * (c.x * P.T - P.S0 * iom) + P.gC1 * (c.y * P.T - P.S1 * iom) +
-                     P.gC2 * (c.z * P.T - P.S2 * iom) + P.gD * (c.w * P.T - P.SD * iom) +
-                     P.gN0 * (nn.x * P.T - P.SN0 * iom) + P.gN1 * (nn.y * P.T - P.SN1 * iom) +
-                     P.gN2 * (nn.z * P.T - P.SN2 * iom);
-  P.S0 = fmaf(w, c.x, P.S0); P.S1 = fmaf(w, c.y, P.S1); P.S2 = fmaf(w, c.z, P.S2); P.SD = fmaf(w, c.w, P.SD);
-  P.SN0 = fmaf(w, nn.x, P.SN0); P.SN1 = fmaf(w, nn.y, P.SN1); P.SN2 = fmaf(w, nn.z, P.SN2);
+  float gf = P.gC0 * c.x;
+  gf = fmaf(P.gC1, c.y, gf); gf = fmaf(P.gC2, c.z, gf); gf = fmaf(P.gD, c.w, gf);
+  gf = fmaf(P.gN0, nn.x, gf); gf = fmaf(P.gN1, nn.y, gf); gf = fmaf(P.gN2, nn.z, gf);
+  const float dLda = fmaf(P.T, gf, -P.GS * iom);
+  P.GS = fmaf(w, gf, P.GS);
   vals[6] = fmaf(w, P.gC0, vals[6]); vals[7] = fmaf(w, P.gC1, vals[7]); vals[8] = fmaf(w, P.gC2, vals[8]);
   vals[9] = fmaf(w, P.gD, vals[9]);
   vals[10] = fmaf(w, P.gN0, vals[10]); vals[11] = fmaf(w, P.gN1, vals[11]); vals[12] = fmaf(w, P.gN2, vals[12]);
-  if (!(a_raw > a_max)) {
-    // d alpha / d power_nat = a_raw; natural conic = scaled / (-1/2 log2 e)
+  if (!(a_raw > a_max)) {            // alpha clamped at alpha_max carries no gradient to o, mean, conic
     const float G = dLda * a_raw;
-    const float An = q.x * (1.f / kHalfLog2e), Bn = q.y * (1.f / kNegLog2e), Cn = q.z * (1.f / kHalfLog2e);
-    vals[0] = fmaf(G, An * dx + Bn * dy, vals[0]);
-    vals[1] = fmaf(G, Bn * dx + Cn * dy, vals[1]);
-    vals[2] = fmaf(-0.5f * G, dx * dx, vals[2]);
-    vals[3] = fmaf(-G, dx * dy, vals[3]);
-    vals[4] = fmaf(-0.5f * G, dy * dy, vals[4]);
-    vals[5] = fmaf(dLda, a_raw / q.w, vals[5]);
+    vals[0] = fmaf(G, dx, vals[0]);
+    vals[1] = fmaf(G, dy, vals[1]);
+    vals[2] = fmaf(G, dx * dx, vals[2]);
+    vals[3] = fmaf(G, dx * dy, vals[3]);
+    vals[4] = fmaf(G, dy * dy, vals[4]);
+    vals[5] += G;
   }
   return true;
 }
 
+// Per-Gaussian gradients from the reduced sums: power_nat = -1/2 (A dx^2 + 2B dx dy + C dy^2)
+// with dx = px - mx, so d/dmx = A dx + B dy, d/dA = -1/2 dx^2, d/dB = -dx dy, d/dC = -1/2 dy^2,
+// and d alpha / d o = alpha_raw / o.
+__device__ __forceinline__ void finish_grads(const float* a, float4 q, float out[13]) {
+  const float An = q.x * (1.f / kHalfLog2e), Bn = q.y * (1.f / kNegLog2e), Cn = q.z * (1.f / kHalfLog2e);
+  out[0] = An * a[0] + Bn * a[1];
+  out[1] = Bn * a[0] + Cn * a[1];
+  out[2] = -0.5f * a[2];
+  out[3] = -a[3];
+  out[4] = -0.5f * a[4];
+  out[5] = a[5] / q.w;
+#pragma unroll
+  for (int f = 6; f < 13; ++f) out[f] = a[f];
+}
+
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2) k_blend_bwd(const __grid_constant__ BatchDev b,
+__global__ void __launch_bounds__(TW * TH / 2, 8) k_blend_bwd(const __grid_constant__ BatchDev b,
                                                            const float4* __restrict__ rec,
                                                            const uint32_t* __restrict__ pair_g,
                                                            const uint2* __restrict__ ranges, pgs_image_ptrs img,
@@ -261,7 +285,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_bwd(const __grid_constant
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
   const int ty = lt / v.tiles_x, tx = lt - ty * v.tiles_x;
-  const int px = tx * TW + (int)threadIdx.x % TW, py0 = ty * TH + 2 * ((int)threadIdx.x / TW);
+  int px, py0;
+  warp_block_pixel<TW>(tx, ty, TH, px, py0);
   const float fx_rel = (float)px + 0.5f - v.cx;
   const int lane = threadIdx.x & 31;
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max;
@@ -316,7 +341,8 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_bwd(const __grid_constant
     for (int h = 0; h < 2; ++h) {
       const int slot = threadIdx.x + h * NT;
       if (slot < cnt) {
-        const float* a = s_acc[slot];
+        float a[13];
+        finish_grads(s_acc[slot], s.q[slot], a);
         float4* dst = reinterpret_cast<float4*>(grad + (size_t)s_g[slot] * 16);
         const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
         const float4 v1 = make_float4(a[4], a[5], a[6], a[7]);
