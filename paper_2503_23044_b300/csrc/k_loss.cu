@@ -18,16 +18,18 @@ struct PixCtx {
   long long p, p3, HW;
 };
 
-__device__ __forceinline__ PixCtx pix_ctx(const BatchDev& b, long long p) {
+// v is a running hint: threads walk increasing pixel indices, so the view only moves forward
+__device__ __forceinline__ PixCtx pix_ctx(const BatchDev& b, long long p, int& v) {
+  while (v + 1 < b.n_views && p >= b.v[v + 1].pix_off) ++v;
   PixCtx c;
-  c.v = view_of_pixel(b, p);
-  const ViewDev& v = b.v[c.v];
-  const long long l = p - v.pix_off;
-  c.py = (int)(l / v.W);
-  c.px = (int)(l - (long long)c.py * v.W);
+  c.v = v;
+  const ViewDev& vw = b.v[v];
+  const unsigned l = (unsigned)(p - vw.pix_off);
+  c.py = (int)(l / (unsigned)vw.W);
+  c.px = (int)(l - (unsigned)c.py * (unsigned)vw.W);
   c.p = p;
-  c.HW = (long long)v.W * v.H;
-  c.p3 = 3 * v.pix_off + l;
+  c.HW = (long long)vw.W * vw.H;
+  c.p3 = 3 * vw.pix_off + l;
   return c;
 }
 
@@ -76,8 +78,9 @@ __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ Bat
   __syncthreads();
   long long s, e;
   range_of_block(b.total_pixels, s, e);
+  int vh = s < e ? view_of_pixel(b, s) : 0;
   for (long long p = s + threadIdx.x; p < e; p += blockDim.x) {
-    const PixCtx c = pix_ctx(b, p);
+    const PixCtx c = pix_ctx(b, p, vh);
     float nd[3], N[3], nn;
     if (tgt.mask[p] > 0.f) atomicAdd(&s_cnt[c.v][0], 1u);
     if (normal_valid(b, c, img, nd, N, nn)) atomicAdd(&s_cnt[c.v][1], 1u);
@@ -99,8 +102,9 @@ __global__ void __launch_bounds__(256) k_loss_grad(const __grid_constant__ Batch
   const float invB = 1.f / (float)b.n_views;
   float l_rgb = 0.f, l_d = 0.f, l_n = 0.f;
   bool bad = false;
+  int vh = s < e ? view_of_pixel(b, s) : 0;
   for (long long p = s + threadIdx.x; p < e; p += blockDim.x) {
-    const PixCtx c = pix_ctx(b, p);
+    const PixCtx c = pix_ctx(b, p, vh);
     const float k_rgb = invB / (3.f * (float)c.HW);
 #pragma unroll
     for (int ch = 0; ch < 3; ++ch) {

@@ -35,6 +35,11 @@ __global__ void k_decode_project(const __grid_constant__ BatchDev b, pgs_anchor_
                                  const uint32_t* rows, const long long* n_rows_p, long long cap, float4* rec,
                                  uint32_t* counts, uint32_t* keys, DecodeOut dec);
 
+// k_decode_tc.cu
+__global__ void k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, pgs_mlp_ptrs Wt,
+                                    const uint32_t* rows, const long long* n_rows_p, long long cap, float4* rec,
+                                    uint32_t* counts, uint32_t* keys, DecodeOut dec, uint32_t* err);
+
 // k_sort.cu
 void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
                            const long long* d_n, unsigned long long* sums, cudaStream_t st);
