@@ -116,10 +116,11 @@ def make_workload(name: str, seed: int, device: str):
     return sc, targets
 
 
-def build_scene(sc, B, device, cap_pairs=None, cap_rows=None):
+def build_scene(sc, B, device, cap_pairs=None, cap_rows=None, precision=None):
     cams = sc["cameras"]
     Na = len(sc["x"])
-    params = B.default_params(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
+    params = B.default_params(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]),
+                              decode_precision=B.DECODE_FP32 if precision is None else precision)
     npix = sum(c.width * c.height for c in cams)
     scene = B.Scene(B.MODE_ANCHOR, Na, len(cams), npix, cap_pairs or (1 << 29),
                     capacity_rows=cap_rows or Na * len(cams), params=params)
@@ -212,7 +213,8 @@ def run_pgs(args):
     cams = sc["cameras"]
     V = len(cams)
     packed = B.pack_cameras(cams)
-    scene, t, pg = build_scene(sc, B, device, args.cap_pairs, args.cap_rows)
+    precision = B.DECODE_BF16 if args.decode == "bf16" else B.DECODE_FP32
+    scene, t, pg = build_scene(sc, B, device, args.cap_pairs, args.cap_rows, precision)
     targets = B.Targets.from_views(tviews, device=device)
     images = B.Images.empty(cams, device=device)
     n_pix = images.offsets[-1]
@@ -295,9 +297,11 @@ def run_pgs(args):
     stats = scene.stats(stream)
     scene.set_profiling(False)
 
-    # plain form: one view per call sequence, eager, no graph
+    # plain form: one view per call sequence, eager, no graph, FP32 decoder
     plain_vps = None
     if not args.no_plain:
+        pscene, _, _ = build_scene(sc, B, device, 1 << 26, len(sc["x"]), B.DECODE_FP32)
+        pscene.bind_anchors(t["x"], t["level"], t["log_l"], t["offsets"], t["feat"], t["W1"], t["b1"], t["W2"], t["b2"])
         pimgs = [B.Images.empty([c], device=device) for c in cams]
         ptg = [B.Targets.from_views([tv], device=device) for tv in tviews]
         pgr = [B.ImageGrads.empty(c.width * c.height, device=device) for c in cams]
@@ -305,9 +309,9 @@ def run_pgs(args):
 
         def plain_step():
             for i, c in enumerate(cams):
-                scene.render([c], pimgs[i], packed=pk[i])
-                scene.loss_grad([c], pimgs[i], ptg[i], loss=loss, grads=pgr[i], packed=pk[i])
-                scene.backward([c], pimgs[i], pgr[i], pg, packed=pk[i])
+                pscene.render([c], pimgs[i], packed=pk[i])
+                pscene.loss_grad([c], pimgs[i], ptg[i], loss=loss, grads=pgr[i], packed=pk[i])
+                pscene.backward([c], pimgs[i], pgr[i], pg, packed=pk[i])
 
         with torch.cuda.stream(stream):
             plain_step()
@@ -324,8 +328,9 @@ def run_pgs(args):
                 e1.record(stream)
             e1.synchronize()
             pm += e0.elapsed_time(e1)
-        scene.read_status(stream)
+        pscene.read_status(stream)
         plain_vps = V * ks / (pm / 1e3)
+        pscene.close()
 
     # end to end through the public API: targets from pinned host memory in,
     # loss scalars out, every step
@@ -390,10 +395,10 @@ def run_pgs(args):
                     data="synthetic",
                     config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
                                 resolution="1600x1064", form="batched: all views per call, CUDA graph" if use_graph
-                                else "batched: all views per call, eager", decode="FP32 SIMT",
+                                else "batched: all views per call, eager", decode="BF16 tcgen05 (FP32 accumulate)" if args.decode == "bf16" else "FP32 SIMT",
                                 tile="16x16", l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"replicas x{world}"),
-                    plain=dict(value=plain_vps, unit="views/s", form="one view per call sequence, eager"),
+                    plain=dict(value=plain_vps, unit="views/s", form="one view per call sequence, eager, FP32 decoder"),
                     e2e=dict(value=e2e_vps, unit="views/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches_per_step * args.steps,
                     roofline=roof, stage_ms=stage_ms, cpu_baseline=cpu, clocks=clocks,
@@ -415,6 +420,7 @@ def main():
     ap.add_argument("--workload", default="batch8_1600")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--decode", default="bf16", choices=("bf16", "fp32"), help="decoder precision of the batched form")
     ap.add_argument("--cap-pairs", type=int, default=None, help="pair capacity (default 2^29)")
     ap.add_argument("--cap-rows", type=int, default=None, help="visible (view, anchor) row capacity")
     args = ap.parse_args()
