@@ -9,6 +9,8 @@
 // rounded operations so that the backward recomputes bit-identical alphas and
 // walks exactly the forward's contributors, from the last one down, undoing
 // the transmittance by division (T_i = T_{i+1} / (1 - alpha_i)).
+#include <algorithm>
+
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
 
@@ -28,14 +30,32 @@ struct BlendSmem {
 
 // The alpha >= alpha_min rule is taken on the exponent, o 2^p >= alpha_min <=>
 // p >= log2(alpha_min / o), so pairs below it never reach the exponential.
-__device__ __forceinline__ void stage_record(BlendSmem& s, int slot, const float4* __restrict__ rec, uint32_t g,
-                                             float a_min) {
+struct RecF {
+  float4 m, q, c, n;   // as in BlendSmem
+};
+__device__ __forceinline__ RecF load_record(const float4* __restrict__ rec, uint32_t g, float a_min) {
   const float4* r = rec + (size_t)g * kRecF4;
   const float4 r0 = __ldg(r), r1 = __ldg(r + 1), r2 = __ldg(r + 2), r3 = __ldg(r + 3);
-  s.m[slot] = r0;
-  s.q[slot] = make_float4(__fmul_rn(r1.x, kHalfLog2e), __fmul_rn(r1.y, kNegLog2e), __fmul_rn(r1.z, kHalfLog2e), r1.w);
-  s.c[slot] = r2;
-  s.n[slot] = make_float4(r3.x, r3.y, r3.z, log2f(__fdiv_rn(a_min, r1.w)));
+  RecF o;
+  o.m = r0;
+  o.q = make_float4(__fmul_rn(r1.x, kHalfLog2e), __fmul_rn(r1.y, kNegLog2e), __fmul_rn(r1.z, kHalfLog2e), r1.w);
+  o.c = r2;
+  o.n = make_float4(r3.x, r3.y, r3.z, log2f(__fdiv_rn(a_min, r1.w)));
+  return o;
+}
+__device__ __forceinline__ void stage_record(BlendSmem& s, int slot, const float4* __restrict__ rec, uint32_t g,
+                                             float a_min) {
+  const RecF r = load_record(rec, g, a_min);
+  s.m[slot] = r.m;
+  s.q[slot] = r.q;
+  s.c[slot] = r.c;
+  s.n[slot] = r.n;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
 }
 
 // power of the Gaussian at the pixel, with the exact operation order shared by both passes
@@ -50,22 +70,24 @@ struct PixF {            // forward state of one pixel
   bool done;
 };
 
-__device__ __forceinline__ void fwd_pair(PixF& P, const BlendSmem& s, int k, uint32_t j, float dx, float4 q, float a_max,
-                                         float t_min) {
-  const float dy = rel_d(P.fy, s.m[k].y, s.m[k].w);
-  const float power = eval_power(q, dx, dy);
-  if (power > 0.f || !(power >= s.n[k].w)) return;
-  const float a_raw = __fmul_rn(q.w, ex2_approx(power));
+// Take (or not) one record at a pixel whose power test gave `take`, with every
+// step predicated: alpha, the stop rule T_new < t_min (the pixel ends before
+// this record) and the masked accumulation.
+__device__ __forceinline__ void fwd_take(PixF& P, bool take, float power, float opac, const float4 c,
+                                         const float4 nn, uint32_t j, float a_max, float t_min) {
+  const float a_raw = __fmul_rn(opac, ex2_approx(power));
   const float alpha = fminf(a_max, a_raw);
   const float Tn = __fmul_rn(P.T, __fsub_rn(1.f, alpha));
-  if (Tn < t_min) { P.done = true; P.stop = j + 1; return; }
-  const float w = __fmul_rn(alpha, P.T);
-  const float4 c = s.c[k], nn = s.n[k];
+  const bool stop = take && Tn < t_min;
+  const bool cont = take && !stop;
+  const float w = cont ? __fmul_rn(alpha, P.T) : 0.f;
   P.cr = fmaf(w, c.x, P.cr); P.cg = fmaf(w, c.y, P.cg); P.cb = fmaf(w, c.z, P.cb); P.D = fmaf(w, c.w, P.D);
   P.n0 = fmaf(w, nn.x, P.n0); P.n1 = fmaf(w, nn.y, P.n1); P.n2 = fmaf(w, nn.z, P.n2);
-  P.T = Tn;
-  P.last = j + 1;
-  ++P.ncontrib;
+  P.T = cont ? Tn : P.T;
+  P.last = cont ? j + 1 : P.last;
+  P.ncontrib += cont ? 1u : 0u;
+  P.stop = stop ? j + 1 : P.stop;
+  P.done = P.done || stop;
 }
 
 __device__ __forceinline__ void fwd_write(const PixF& P, const ViewDev& v, const ParamsDev& p, int px, int py,
@@ -103,14 +125,11 @@ __device__ __forceinline__ void warp_block_pixel(int tx, int ty, int TH, int& px
   py0 = ty * TH + (w / WX) * 8 + 2 * (l >> 3);
 }
 template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant__ BatchDev b,
-                                                           const float4* __restrict__ rec,
-                                                           const uint32_t* __restrict__ pair_g,
-                                                           const uint2* __restrict__ ranges, pgs_image_ptrs out) {
+__device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, BlendSmem& s,
+                                               const float4* __restrict__ rec, const uint32_t* __restrict__ pair_g,
+                                               const uint2* __restrict__ ranges, const pgs_image_ptrs& out) {
   constexpr int NT = TW * TH / 2;
   static_assert(2 * NT == kBatch, "two records per thread per round");
-  __shared__ BlendSmem s;
-  const int tile = blockIdx.x;
   const int vi = view_of_tile(b, tile);
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
@@ -131,49 +150,25 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant
     __syncthreads();
     const int cnt = min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt; ++k) {
-      if (P0.done && P1.done) break;
+      if (__all_sync(0xffffffffu, P0.done && P1.done)) break;
       const float4 q = s.q[k];
-      const float dx = rel_d(fx_rel, s.m[k].x, s.m[k].z);
+      const float4 m = s.m[k];
+      const float p_lo = s.n[k].w;
+      const float dx = rel_d(fx_rel, m.x, m.z);
+      const float pw0 = eval_power(q, dx, rel_d(P0.fy, m.y, m.w));
+      const float pw1 = eval_power(q, dx, rel_d(P1.fy, m.y, m.w));
+      // skip power > 0 and alpha < alpha_min (taken on the exponent); the warp skips a record none of its pixels takes
+      const bool t0 = !P0.done && !(pw0 > 0.f) && pw0 >= p_lo;
+      const bool t1 = !P1.done && !(pw1 > 0.f) && pw1 >= p_lo;
+      if (!__any_sync(0xffffffffu, t0 || t1)) continue;
+      const float4 c = s.c[k], nn = s.n[k];
       const uint32_t j = start + k;
-      if (!P0.done) fwd_pair(P0, s, k, j, dx, q, a_max, t_min);
-      if (!P1.done) fwd_pair(P1, s, k, j, dx, q, a_max, t_min);
+      fwd_take(P0, t0, pw0, q.w, c, nn, j, a_max, t_min);
+      fwd_take(P1, t1, pw1, q.w, c, nn, j, a_max, t_min);
     }
   }
   fwd_write(P0, v, b.p, px, py0, fx_rel, rg.x, out);
   fwd_write(P1, v, b.p, px, py0 + 1, fx_rel, rg.x, out);
-}
-
-// Lane-distributed sum of 16 slots across a warp with 16 shuffles: afterwards
-// lane l holds the warp total of slot (l >> 1) & 15.
-__device__ __forceinline__ float warp_transpose_reduce16(float v[16], int lane) {
-#pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const bool up = lane & 16;
-    const float send = up ? v[i] : v[i + 8];
-    const float keep = up ? v[i + 8] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
-  }
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const bool up = lane & 8;
-    const float send = up ? v[i] : v[i + 4];
-    const float keep = up ? v[i + 4] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 8);
-  }
-#pragma unroll
-  for (int i = 0; i < 2; ++i) {
-    const bool up = lane & 4;
-    const float send = up ? v[i] : v[i + 2];
-    const float keep = up ? v[i + 2] : v[i];
-    v[i] = keep + __shfl_xor_sync(0xffffffffu, send, 4);
-  }
-  {
-    const bool up = lane & 2;
-    const float send = up ? v[0] : v[1];
-    const float keep = up ? v[1] : v[0];
-    v[0] = keep + __shfl_xor_sync(0xffffffffu, send, 2);
-  }
-  return v[0] + __shfl_xor_sync(0xffffffffu, v[0], 1);
 }
 
 struct PixB {            // backward state of one pixel
@@ -214,43 +209,6 @@ __device__ __forceinline__ void bwd_setup(PixB& P, const ViewDev& v, const Param
   P.GS = P.T * p.bg * (P.gC0 + P.gC1 + P.gC2);
 }
 
-// Undo one contributor of the pixel (back to front) and add its per-pixel sums
-// into vals; returns false if the pair did not contribute in the forward.
-//   vals[0..5]  = sum G dx, G dy, G dx^2, G dx dy, G dy^2, G   (G = dL/dalpha * alpha_raw)
-//   vals[6..12] = sum w gC (3), w gD, w gN (3)
-// dL/dalpha_i = T_i (g . f_i) - (g . S_i) / (1 - alpha_i), with g . S_i carried as one scalar.
-__device__ __forceinline__ bool bwd_pair(PixB& P, const BlendSmem& s, int k, float dx, float4 q, float a_max,
-                                         float vals[16]) {
-  const float dy = rel_d(P.fy, s.m[k].y, s.m[k].w);
-  const float power = eval_power(q, dx, dy);
-  const float4 nn = s.n[k];
-  if (power > 0.f || !(power >= nn.w)) return false;
-  const float a_raw = __fmul_rn(q.w, ex2_approx(power));
-  const float alpha = fminf(a_max, a_raw);
-  const float iom = 1.f / __fsub_rn(1.f, alpha);
-  P.T = P.T * iom;
-  const float w = alpha * P.T;
-  const float4 c = s.c[k];
-  float gf = P.gC0 * c.x;
-  gf = fmaf(P.gC1, c.y, gf); gf = fmaf(P.gC2, c.z, gf); gf = fmaf(P.gD, c.w, gf);
-  gf = fmaf(P.gN0, nn.x, gf); gf = fmaf(P.gN1, nn.y, gf); gf = fmaf(P.gN2, nn.z, gf);
-  const float dLda = fmaf(P.T, gf, -P.GS * iom);
-  P.GS = fmaf(w, gf, P.GS);
-  vals[6] = fmaf(w, P.gC0, vals[6]); vals[7] = fmaf(w, P.gC1, vals[7]); vals[8] = fmaf(w, P.gC2, vals[8]);
-  vals[9] = fmaf(w, P.gD, vals[9]);
-  vals[10] = fmaf(w, P.gN0, vals[10]); vals[11] = fmaf(w, P.gN1, vals[11]); vals[12] = fmaf(w, P.gN2, vals[12]);
-  if (!(a_raw > a_max)) {            // alpha clamped at alpha_max carries no gradient to o, mean, conic
-    const float G = dLda * a_raw;
-    vals[0] = fmaf(G, dx, vals[0]);
-    vals[1] = fmaf(G, dy, vals[1]);
-    vals[2] = fmaf(G, dx * dx, vals[2]);
-    vals[3] = fmaf(G, dx * dy, vals[3]);
-    vals[4] = fmaf(G, dy * dy, vals[4]);
-    vals[5] += G;
-  }
-  return true;
-}
-
 // Per-Gaussian gradients from the reduced sums: power_nat = -1/2 (A dx^2 + 2B dx dy + C dy^2)
 // with dx = px - mx, so d/dmx = A dx + B dy, d/dA = -1/2 dx^2, d/dB = -dx dy, d/dC = -1/2 dy^2,
 // and d alpha / d o = alpha_raw / o.
@@ -266,126 +224,243 @@ __device__ __forceinline__ void finish_grads(const float* a, float4 q, float out
   for (int f = 6; f < 13; ++f) out[f] = a[f];
 }
 
-template <int TW, int TH>
-__global__ void __launch_bounds__(TW * TH / 2, 8) k_blend_bwd(const __grid_constant__ BatchDev b,
-                                                           const float4* __restrict__ rec,
-                                                           const uint32_t* __restrict__ pair_g,
-                                                           const uint2* __restrict__ ranges, pgs_image_ptrs img,
-                                                           pgs_image_grad_ptrs gi, float* __restrict__ grad) {
-  constexpr int NT = TW * TH / 2;
-  static_assert(2 * NT == kBatch, "two records per thread per round");
-  __shared__ BlendSmem s;
-  __shared__ float s_acc[kBatch][kGradFields];
-  __shared__ uint32_t s_g[kBatch];
-  __shared__ int s_max;
-  const int tile = blockIdx.x;
+// Backward, record-parallel within the tile: one warp per tile.  The tile's
+// list is taken back to front in chunks of up to 32 records, lane l holding
+// record cbase + l.  The pixels that still have contributors at or below the
+// chunk's top (last > cbase) stream through the lanes from the top lane down
+// to lane 0, one lane per step, so each pixel meets the chunk's records in
+// descending order as the reverse pass requires.  A pixel's running state
+// (T, GS) moves down one lane per step by shuffle and is parked in shared
+// memory between chunks.  Each lane sums its own record's per-pixel terms in
+// registers (no cross-lane reduction) and adds the record's gradient to
+// global memory once per (record, tile).
+//   acc[0..5]  = sum G dx, G dy, G dx^2, G dx dy, G dy^2, G   (G = dL/dalpha * alpha_raw)
+//   acc[6..12] = sum w gC (3), w gD, w gN (3)
+// dL/dalpha_i = T_i (g . f_i) - (g . S_i) / (1 - alpha_i), with g . S_i carried as one scalar GS.
+constexpr int kBwdWarps = 2;     // warps per CTA, each on its own tile
+constexpr int kTilePix = 256;
+
+struct BwdTab {                  // per pixel of the tile, in pixel order
+  float4 g0[kTilePix];           // dL/dC (3), dL/dD
+  float4 g1[kTilePix];           // dL/dN (3), last contributor + 1 (bits)
+  float2 f[kTilePix];            // pixel centre relative to the principal point
+  float2 st[kTilePix];           // running (T, GS)
+  uint8_t live[kTilePix];        // pixels still live in the current chunk
+};
+
+template <int TW>
+__device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdTab& tab,
+                                               const float4* __restrict__ rec, const uint32_t* __restrict__ pair_g,
+                                               const uint2* __restrict__ ranges, const pgs_image_ptrs& img,
+                                               const pgs_image_grad_ptrs& gi, float* __restrict__ grad) {
+  constexpr unsigned FULL = 0xffffffffu;
+  constexpr int TH = kTilePix / TW;
+  const int lane = threadIdx.x & 31;
   const uint2 rg = ranges[tile];
   if (rg.y <= rg.x) return;
   const int vi = view_of_tile(b, tile);
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
   const int ty = lt / v.tiles_x, tx = lt - ty * v.tiles_x;
-  int px, py0;
-  warp_block_pixel<TW>(tx, ty, TH, px, py0);
-  const float fx_rel = (float)px + 0.5f - v.cx;
-  const int lane = threadIdx.x & 31;
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max;
-  PixB P0, P1;
-  bwd_setup(P0, v, b.p, px, py0, fx_rel, img, gi);
-  bwd_setup(P1, v, b.p, px, py0 + 1, fx_rel, img, gi);
-  if (threadIdx.x == 0) s_max = 0;
-  __syncthreads();
-  atomicMax(&s_max, (int)max(P0.last, P1.last));
-  __syncthreads();
-  const uint32_t end = (uint32_t)s_max;   // 1 + last contributor index over the tile
-  for (uint32_t bend = end; bend > rg.x;) {
-    const uint32_t bstart = bend > rg.x + kBatch ? bend - kBatch : rg.x;
-    const int cnt = (int)(bend - bstart);
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int slot = threadIdx.x + h * NT;
-      if (slot < cnt) {
-        const uint32_t g = pair_g[bstart + slot];
-        s_g[slot] = g;
-        stage_record(s, slot, rec, g, a_min);
-#pragma unroll
-        for (int f = 0; f < kGradFields; ++f) s_acc[slot][f] = 0.f;
-      }
-    }
-    __syncthreads();
-    // the warp walks from its highest live index down
-    const int my_top = (int)min(max(P0.last, P1.last), bend) - 1 - (int)bstart;
-    const int top = __reduce_max_sync(0xffffffffu, my_top);
-    for (int k = top; k >= 0; --k) {
-      const uint32_t j = bstart + k;
-      float vals[16];
-#pragma unroll
-      for (int f = 0; f < 16; ++f) vals[f] = 0.f;
-      bool contrib = false;
-      const bool live0 = j < P0.last, live1 = j < P1.last;
-      if (live0 || live1) {
-        const float4 q = s.q[k];
-        const float dx = rel_d(fx_rel, s.m[k].x, s.m[k].z);
-        if (live0) contrib |= bwd_pair(P0, s, k, dx, q, a_max, vals);
-        if (live1) contrib |= bwd_pair(P1, s, k, dx, q, a_max, vals);
-      }
-      if (__any_sync(0xffffffffu, contrib)) {
-        const float r = warp_transpose_reduce16(vals, lane);
-        const int slot = (lane >> 1) & 15;
-        if (!(lane & 1) && slot < kGradFields) atomicAdd(&s_acc[k][slot], r);
-      }
-    }
-    __syncthreads();
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int slot = threadIdx.x + h * NT;
-      if (slot < cnt) {
-        float a[13];
-        finish_grads(s_acc[slot], s.q[slot], a);
-        float4* dst = reinterpret_cast<float4*>(grad + (size_t)s_g[slot] * 16);
-        const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
-        const float4 v1 = make_float4(a[4], a[5], a[6], a[7]);
-        const float4 v2 = make_float4(a[8], a[9], a[10], a[11]);
-        if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(dst, v0);
-        if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f || v1.w != 0.f) atomicAdd(dst + 1, v1);
-        if (v2.x != 0.f || v2.y != 0.f || v2.z != 0.f || v2.w != 0.f) atomicAdd(dst + 2, v2);
-        if (a[12] != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 3), a[12]);
-      }
-    }
-    bend = bstart;
+  uint32_t end = 0;
+  for (int p = lane; p < kTilePix; p += 32) {
+    const int px = tx * TW + p % TW, py = ty * TH + p / TW;
+    const float fx = (float)px + 0.5f - v.cx;
+    PixB P;
+    bwd_setup(P, v, b.p, px, py, fx, img, gi);
+    tab.g0[p] = make_float4(P.gC0, P.gC1, P.gC2, P.gD);
+    tab.g1[p] = make_float4(P.gN0, P.gN1, P.gN2, __uint_as_float(P.last));
+    tab.f[p] = make_float2(fx, P.fy);
+    tab.st[p] = make_float2(P.T, P.GS);
+    end = max(end, P.last);
   }
+  end = min(__reduce_max_sync(FULL, end), rg.y);   // a stale `last` never walks past the tile's list
+  for (uint32_t cend = end; cend > rg.x;) {
+    const uint32_t cbase = cend > rg.x + 32 ? cend - 32 : rg.x;
+    const int top = (int)(cend - cbase) - 1;   // lane of the chunk's last record
+    __syncwarp();
+    int n_live = 0;
+#pragma unroll
+    for (int p0 = 0; p0 < kTilePix; p0 += 32) {
+      const bool lv = __float_as_uint(tab.g1[p0 + lane].w) > cbase;
+      const unsigned m = __ballot_sync(FULL, lv);
+      if (lv) tab.live[n_live + __popc(m & ((1u << lane) - 1u))] = (uint8_t)(p0 + lane);
+      n_live += __popc(m);
+    }
+    const uint32_t j = cbase + lane;
+    const bool has = lane <= top;
+    uint32_t gid = 0;
+    RecF r{};
+    if (has) {
+      gid = pair_g[j];
+      r = load_record(rec, gid, a_min);
+    }
+    float acc[kGradFields];
+#pragma unroll
+    for (int f = 0; f < kGradFields; ++f) acc[f] = 0.f;
+    __syncwarp();
+    float T = 0.f, GS = 0.f;
+    const int nsteps = n_live + top;
+    // Branch-free step: every lane evaluates its pair and masks what it does
+    // not take, so consecutive steps can overlap (only T and GS are carried).
+#pragma unroll 2
+    for (int s = 0; s < nsteps; ++s) {
+      const int pi = s - top + lane;
+      const bool act = has && (unsigned)pi < (unsigned)n_live;
+      const int pix = tab.live[act ? pi : 0];
+      const float4 g1 = tab.g1[pix];
+      const float2 f = tab.f[pix];
+      const float4 g0 = tab.g0[pix];
+      float Tin = __shfl_down_sync(FULL, T, 1);
+      float GSin = __shfl_down_sync(FULL, GS, 1);
+      if (lane == top) {
+        const float2 t = tab.st[pix];
+        Tin = t.x;
+        GSin = t.y;
+      }
+      const float dx = rel_d(f.x, r.m.x, r.m.z), dy = rel_d(f.y, r.m.y, r.m.w);
+      const float power = eval_power(r.q, dx, dy);
+      const bool take = act && j < __float_as_uint(g1.w) && !(power > 0.f) && power >= r.n.w;
+      const float a_raw = __fmul_rn(r.q.w, ex2_approx(power));
+      const float alpha = fminf(a_max, a_raw);
+      const float iom = rcp_approx(__fsub_rn(1.f, alpha));
+      T = take ? Tin * iom : Tin;
+      const float w = take ? alpha * T : 0.f;
+      float gf = g0.x * r.c.x;
+      gf = fmaf(g0.y, r.c.y, gf); gf = fmaf(g0.z, r.c.z, gf); gf = fmaf(g0.w, r.c.w, gf);
+      gf = fmaf(g1.x, r.n.x, gf); gf = fmaf(g1.y, r.n.y, gf); gf = fmaf(g1.z, r.n.z, gf);
+      const float dLda = fmaf(T, gf, -GSin * iom);
+      GS = fmaf(w, gf, GSin);
+      acc[6] = fmaf(w, g0.x, acc[6]); acc[7] = fmaf(w, g0.y, acc[7]); acc[8] = fmaf(w, g0.z, acc[8]);
+      acc[9] = fmaf(w, g0.w, acc[9]);
+      acc[10] = fmaf(w, g1.x, acc[10]); acc[11] = fmaf(w, g1.y, acc[11]); acc[12] = fmaf(w, g1.z, acc[12]);
+      // alpha clamped at alpha_max carries no gradient to o, mean, conic
+      const float G = (take && !(a_raw > a_max)) ? dLda * a_raw : 0.f;
+      acc[0] = fmaf(G, dx, acc[0]);
+      acc[1] = fmaf(G, dy, acc[1]);
+      acc[2] = fmaf(G, dx * dx, acc[2]);
+      acc[3] = fmaf(G, dx * dy, acc[3]);
+      acc[4] = fmaf(G, dy * dy, acc[4]);
+      acc[5] += G;
+      if (act && lane == 0) tab.st[pix] = make_float2(T, GS);
+    }
+    if (has) {
+      float a[kGradFields];
+      finish_grads(acc, r.q, a);
+      float4* dst = reinterpret_cast<float4*>(grad + (size_t)gid * 16);
+      const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
+      const float4 v1 = make_float4(a[4], a[5], a[6], a[7]);
+      const float4 v2 = make_float4(a[8], a[9], a[10], a[11]);
+      if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(dst, v0);
+      if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f || v1.w != 0.f) atomicAdd(dst + 1, v1);
+      if (v2.x != 0.f || v2.y != 0.f || v2.z != 0.f || v2.w != 0.f) atomicAdd(dst + 2, v2);
+      if (a[12] != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 3), a[12]);
+    }
+    cend = cbase;
+  }
+}
+// Persistent kernels: one resident wave of CTAs takes tiles from a global queue
+// in the given order (longest lists first), so long tiles do not form a tail.
+template <int TW, int TH>
+__global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant__ BatchDev b,
+                                                           const float4* __restrict__ rec,
+                                                           const uint32_t* __restrict__ pair_g,
+                                                           const uint2* __restrict__ ranges, pgs_image_ptrs out,
+                                                           const uint32_t* __restrict__ order,
+                                                           uint32_t* __restrict__ counter) {
+  __shared__ BlendSmem s;
+  __shared__ uint32_t s_next;
+  for (;;) {
+    __syncthreads();
+    if (threadIdx.x == 0) s_next = atomicAdd(counter, 1u);
+    __syncthreads();
+    const uint32_t it = s_next;
+    if (it >= (uint32_t)b.total_tiles) break;
+    blend_fwd_tile<TW, TH>(b, (int)order[it], s, rec, pair_g, ranges, out);
+  }
+}
+
+// Backward: every warp takes its own tiles from the queue.
+template <int TW>
+__global__ void __launch_bounds__(32 * kBwdWarps) k_blend_bwd(const __grid_constant__ BatchDev b,
+                                                             const float4* __restrict__ rec,
+                                                             const uint32_t* __restrict__ pair_g,
+                                                             const uint2* __restrict__ ranges, pgs_image_ptrs img,
+                                                             pgs_image_grad_ptrs gi, float* __restrict__ grad,
+                                                             const uint32_t* __restrict__ order,
+                                                             uint32_t* __restrict__ counter) {
+  __shared__ BwdTab tabs[kBwdWarps];
+  BwdTab& tab = tabs[threadIdx.x >> 5];
+  for (;;) {
+    uint32_t it = 0;
+    if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1u);
+    it = __shfl_sync(0xffffffffu, it, 0);
+    if (it >= (uint32_t)b.total_tiles) break;
+    blend_bwd_tile<TW>(b, (int)order[it], tab, rec, pair_g, ranges, img, gi, grad);
+  }
+}
+
+// one resident wave: SMs x CTAs per SM, queried once per kernel instantiation
+template <int TW, int TH, bool BWD, typename K>
+static int resident_grid(K kernel, int threads, int total) {
+  static int per_sm = -1, sms = 0;
+  if (per_sm < 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
+      per_sm = 1;
+  }
+  return std::max(1, std::min(total, per_sm * sms));
 }
 
 template <int TW, int TH>
 static void launch_fwd_t(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                         const pgs_image_ptrs& o, cudaStream_t st) {
-  k_blend_fwd<TW, TH><<<b.total_tiles, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o);
+                         const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
+  const int grid = resident_grid<TW, TH, false>(k_blend_fwd<TW, TH>, TW * TH / 2, b.total_tiles);
+  k_blend_fwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
 }
 template <int TW, int TH>
 static void launch_bwd_t(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                         const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, cudaStream_t st) {
-  k_blend_bwd<TW, TH><<<b.total_tiles, TW * TH / 2, 0, st>>>(b, rec, pg, rg, img, gi, grad);
+                         const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, const uint32_t* order,
+                         uint32_t* ctr, cudaStream_t st) {
+  static_assert(TW * TH == kTilePix, "256-pixel tiles");
+  const int grid = resident_grid<TW, TH, true>(k_blend_bwd<TW>, 32 * kBwdWarps,
+                                              (b.total_tiles + kBwdWarps - 1) / kBwdWarps);
+  k_blend_bwd<TW><<<grid, 32 * kBwdWarps, 0, st>>>(b, rec, pg, rg, img, gi, grad, order, ctr);
 }
 
 bool launch_blend_fwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                      const pgs_image_ptrs& o, cudaStream_t st) {
+                      const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
   const int tw = b.p.tile_w, th = b.p.tile_h;
-  if (tw == 16 && th == 16) launch_fwd_t<16, 16>(b, rec, pg, rg, o, st);
-  else if (tw == 8 && th == 32) launch_fwd_t<8, 32>(b, rec, pg, rg, o, st);
-  else if (tw == 32 && th == 8) launch_fwd_t<32, 8>(b, rec, pg, rg, o, st);
+  if (tw == 16 && th == 16) launch_fwd_t<16, 16>(b, rec, pg, rg, o, order, ctr, st);
+  else if (tw == 8 && th == 32) launch_fwd_t<8, 32>(b, rec, pg, rg, o, order, ctr, st);
+  else if (tw == 32 && th == 8) launch_fwd_t<32, 8>(b, rec, pg, rg, o, order, ctr, st);
   else return false;
   return true;
 }
 
 bool launch_blend_bwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                      const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, cudaStream_t st) {
+                      const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, const uint32_t* order,
+                      uint32_t* ctr, cudaStream_t st) {
   const int tw = b.p.tile_w, th = b.p.tile_h;
-  if (tw == 16 && th == 16) launch_bwd_t<16, 16>(b, rec, pg, rg, img, gi, grad, st);
-  else if (tw == 8 && th == 32) launch_bwd_t<8, 32>(b, rec, pg, rg, img, gi, grad, st);
-  else if (tw == 32 && th == 8) launch_bwd_t<32, 8>(b, rec, pg, rg, img, gi, grad, st);
+  if (tw == 16 && th == 16) launch_bwd_t<16, 16>(b, rec, pg, rg, img, gi, grad, order, ctr, st);
+  else if (tw == 8 && th == 32) launch_bwd_t<8, 32>(b, rec, pg, rg, img, gi, grad, order, ctr, st);
+  else if (tw == 32 && th == 8) launch_bwd_t<32, 8>(b, rec, pg, rg, img, gi, grad, order, ctr, st);
   else return false;
   return true;
+}
+
+// Queue order of the tiles: descending list length (ties keep tile order).
+__global__ void k_tile_order_keys(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
+                                  uint32_t* __restrict__ vals) {
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
+    const uint2 r = ranges[t];
+    const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
+    keys[t] = 0xffffffu - min(len, 0xffffffu);
+    vals[t] = (uint32_t)t;
+  }
 }
 
 }  // namespace pgs

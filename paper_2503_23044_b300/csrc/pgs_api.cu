@@ -83,10 +83,12 @@ struct pgs_scene {
   uint32_t* offs = nullptr;
   uint32_t *ptile_a = nullptr, *ptile_b = nullptr, *pg_a = nullptr, *pg_b = nullptr;
   uint2* ranges = nullptr;
+  uint32_t *order_k = nullptr, *order_v = nullptr, *order_kb = nullptr, *order_vb = nullptr;  // tile queue
+  uint32_t* queue_ctr = nullptr;         // [0] forward, [1] backward
   uint32_t *cull_flags = nullptr, *cull_offs = nullptr, *rows = nullptr;
   float *sc_dZ = nullptr, *sc_H = nullptr, *sc_dH = nullptr, *sc_X = nullptr, *wg_partials = nullptr;
   int wg_blocks = 0;
-  long long* d_cnt = nullptr;            // [0] rows, [1] G, [2] P, [3] cull items
+  long long* d_cnt = nullptr;            // [0] rows, [1] G, [2] P, [3] cull items, [4] tiles
   unsigned long long* d_tot = nullptr;   // [0] cull total, [1] pair total
   unsigned long long* scan_sums = nullptr;
   void* sort_mem = nullptr;
@@ -154,7 +156,8 @@ void pgs_scene_destroy(pgs_scene* s) {
   void* ps[] = {s->rec, s->grad_rec, s->counts, s->keys_a, s->keys_b, s->gid_a, s->gid_b, s->offs, s->ptile_a,
                 s->ptile_b, s->pg_a, s->pg_b, s->ranges, s->cull_flags, s->cull_offs, s->rows, s->sc_dZ, s->sc_H,
                 s->sc_dH, s->sc_X, s->wg_partials, s->d_cnt, s->d_tot, s->scan_sums, s->sort_mem, s->d_flags,
-                s->loss_counts, s->loss_partials};
+                s->loss_counts, s->loss_partials, s->order_k, s->order_v, s->order_kb, s->order_vb,
+                s->queue_ctr};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : s->ev)
@@ -198,7 +201,7 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   s->cap_pairs = d.capacity_pairs;
   s->max_tiles = d.max_pixels / 64 + (long long)d.max_views * 1024;
   s->n_cull = d.mode == PGS_MODE_ANCHOR ? N * d.max_views : 0;
-  const long long sort_n = std::max(s->cap_g, s->cap_pairs);
+  const long long sort_n = std::max(std::max(s->cap_g, s->cap_pairs), s->max_tiles);
   s->ss = sort_scratch_layout(nullptr, sort_n);
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n) if (e == cudaSuccess) e = dmalloc(&(ptr), (size_t)(n))
@@ -215,6 +218,11 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   ALLOC(s->pg_a, s->cap_pairs);
   ALLOC(s->pg_b, s->cap_pairs);
   ALLOC(s->ranges, s->max_tiles);
+  ALLOC(s->order_k, s->max_tiles);
+  ALLOC(s->order_v, s->max_tiles);
+  ALLOC(s->order_kb, s->max_tiles);
+  ALLOC(s->order_vb, s->max_tiles);
+  ALLOC(s->queue_ctr, 2);
   ALLOC(s->d_cnt, 8);
   ALLOC(s->d_tot, 4);
   ALLOC(s->scan_sums, kScanBlocks);
@@ -418,9 +426,17 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
   PGS_CUDA(cudaMemsetAsync(s->ranges, 0, (size_t)b.total_tiles * sizeof(uint2), st));
   k_tile_ranges<<<ns * 8, 256, 0, st>>>(s->ptile_a, d_P, s->ranges);
   s->launches += nl + 1;
+  // queue order for the persistent blend kernels: longest tile lists first
+  k_set_i64<<<1, 1, 0, st>>>(s->d_cnt + 4, b.total_tiles);
+  k_tile_order_keys<<<ns * 2, 256, 0, st>>>(s->ranges, b.total_tiles, s->order_k, s->order_v);
+  PGS_CUDA(launch_sort_pairs(s->order_k, s->order_v, s->order_kb, s->order_vb, s->d_cnt + 4, s->max_tiles, 0, 24,
+                             s->ss, s->d_flags, s->spin_limit, ns, st, &nl));
+  s->launches += 2 + nl;
   prof_mark(s, PGS_STAGE_TILE_SORT, 1, st);
   prof_mark(s, PGS_STAGE_BLEND_FWD, 0, st);
-  if (!launch_blend_fwd(b, s->rec, s->pg_a, s->ranges, *out, st)) return fail(PGS_ERR_UNSUPPORTED, "tile shape");
+  PGS_CUDA(cudaMemsetAsync(s->queue_ctr, 0, 2 * sizeof(uint32_t), st));
+  if (!launch_blend_fwd(b, s->rec, s->pg_a, s->ranges, *out, s->order_v, s->queue_ctr, st))
+    return fail(PGS_ERR_UNSUPPORTED, "tile shape");
   s->launches += 1;
   prof_mark(s, PGS_STAGE_BLEND_FWD, 1, st);
   PGS_CUDA(cudaGetLastError());
@@ -462,7 +478,8 @@ pgs_status pgs_backward(pgs_scene* s, const pgs_camera* cams, int n_views, const
   const long long* d_G = s->d_cnt + 1;
   prof_mark(s, PGS_STAGE_BLEND_BWD, 0, st);
   k_zero_f4<<<ns * 4, 256, 0, st>>>(reinterpret_cast<float4*>(s->grad_rec), d_G, 4);
-  if (!launch_blend_bwd(b, s->rec, s->pg_a, s->ranges, *img, *grad, s->grad_rec, st))
+  PGS_CUDA(cudaMemsetAsync(s->queue_ctr + 1, 0, sizeof(uint32_t), st));
+  if (!launch_blend_bwd(b, s->rec, s->pg_a, s->ranges, *img, *grad, s->grad_rec, s->order_v, s->queue_ctr + 1, st))
     return fail(PGS_ERR_UNSUPPORTED, "tile shape");
   s->launches += 2;
   prof_mark(s, PGS_STAGE_BLEND_BWD, 1, st);

@@ -56,11 +56,13 @@ __global__ void k_emit_pairs(const __grid_constant__ BatchDev b, const float4* r
 __global__ void k_pairs_total(const unsigned long long* total, long long cap, long long* d_p, uint32_t* err);
 __global__ void k_tile_ranges(const uint32_t* tiles, const long long* d_p, uint2* ranges);
 
-// k_blend.cu
+// k_blend.cu (persistent kernels: tiles taken from a queue in `order` via `ctr`, which must start at 0)
 bool launch_blend_fwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                      const pgs_image_ptrs& o, cudaStream_t st);
+                      const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st);
 bool launch_blend_bwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
-                      const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, cudaStream_t st);
+                      const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, const uint32_t* order,
+                      uint32_t* ctr, cudaStream_t st);
+__global__ void k_tile_order_keys(const uint2* ranges, int n_tiles, uint32_t* keys, uint32_t* vals);
 
 // k_loss.cu
 void launch_loss(const BatchDev& b, const pgs_image_ptrs& img, const pgs_target_ptrs& tgt, const pgs_loss_params& lp,
