@@ -22,7 +22,7 @@ constexpr float kNegLog2e = -kLog2e;
 constexpr int kBatch = 256;   // records staged per round (two per thread)
 
 struct BlendSmem {
-  float4 m[kBatch];    // mean (hi x, hi y, lo x, lo y)
+  float2 m[kBatch];    // mean relative to the block origin
   float4 q[kBatch];    // (A', B', C', opacity)
   float4 c[kBatch];    // (r, g, b, d)
   float4 n[kBatch];    // (nx, ny, nz, p_lo): p_lo = log2(alpha_min / opacity)
@@ -31,7 +31,7 @@ struct BlendSmem {
 // The alpha >= alpha_min rule is taken on the exponent, o 2^p >= alpha_min <=>
 // p >= log2(alpha_min / o), so pairs below it never reach the exponential.
 struct RecF {
-  float4 m, q, c, n;   // as in BlendSmem
+  float4 m, q, c, n;   // m: mean relative to the principal point (hi x, hi y, lo x, lo y); q, c, n as in BlendSmem
 };
 __device__ __forceinline__ RecF load_record(const float4* __restrict__ rec, uint32_t g, float a_min) {
   const float4* r = rec + (size_t)g * kRecF4;
@@ -43,10 +43,20 @@ __device__ __forceinline__ RecF load_record(const float4* __restrict__ rec, uint
   o.n = make_float4(r3.x, r3.y, r3.z, log2f(__fdiv_rn(a_min, r1.w)));
   return o;
 }
+// Mean relative to a block origin (ox, oy), both relative to the principal
+// point: one rounded expression shared by both passes, so that their pixel
+// offsets dx = (px_local + 1/2) - m_t agree bit for bit.  The origin is that
+// of the 32 x 32 pixel block holding the tile, so every supported tile shape
+// gives a pixel the same offsets (and the same image).
+constexpr int kOriginBlock = 32;
+__device__ __forceinline__ int block_origin(int p0) { return p0 & ~(kOriginBlock - 1); }
+__device__ __forceinline__ float2 tile_mean(const float4 m, float ox, float oy) {
+  return make_float2(__fadd_rn(__fsub_rn(m.x, ox), m.z), __fadd_rn(__fsub_rn(m.y, oy), m.w));
+}
 __device__ __forceinline__ void stage_record(BlendSmem& s, int slot, const float4* __restrict__ rec, uint32_t g,
-                                             float a_min) {
+                                             float a_min, float ox, float oy) {
   const RecF r = load_record(rec, g, a_min);
-  s.m[slot] = r.m;
+  s.m[slot] = tile_mean(r.m, ox, oy);
   s.q[slot] = r.q;
   s.c[slot] = r.c;
   s.n[slot] = r.n;
@@ -62,10 +72,9 @@ __device__ __forceinline__ float rcp_approx(float x) {
 __device__ __forceinline__ float eval_power(const float4 q, float dx, float dy) {
   return __fmaf_rn(q.x, __fmul_rn(dx, dx), __fmaf_rn(q.z, __fmul_rn(dy, dy), __fmul_rn(q.y, __fmul_rn(dx, dy))));
 }
-__device__ __forceinline__ float rel_d(float f_rel, float hi, float lo) { return __fsub_rn(__fsub_rn(f_rel, hi), lo); }
 
 struct PixF {            // forward state of one pixel
-  float fy, T, cr, cg, cb, D, n0, n1, n2;
+  float T, cr, cg, cb, D, n0, n1, n2;
   uint32_t last, ncontrib, stop;
   bool done;
 };
@@ -91,8 +100,9 @@ __device__ __forceinline__ void fwd_take(PixF& P, bool take, float power, float 
 }
 
 __device__ __forceinline__ void fwd_write(const PixF& P, const ViewDev& v, const ParamsDev& p, int px, int py,
-                                          float fx_rel, uint32_t lo, const pgs_image_ptrs& out) {
+                                          uint32_t lo, const pgs_image_ptrs& out) {
   if (px >= v.W || py >= v.H) return;
+  const float fx_rel = (float)px + 0.5f - v.cx, fy_rel = (float)py + 0.5f - v.cy;
   const long long HW = (long long)v.W * v.H;
   const long long q = v.pix_off + (long long)py * v.W + px;
   const long long q3 = 3 * v.pix_off + (long long)py * v.W + px;
@@ -103,7 +113,7 @@ __device__ __forceinline__ void fwd_write(const PixF& P, const ViewDev& v, const
   out.normal[q3 + HW] = P.n1;
   out.normal[q3 + 2 * HW] = P.n2;
   // Eq. 7 with guards: |N . r| >= 1e-8 and accumulated weight >= 1e-6, else 0
-  const float rx = fx_rel / v.fx, ry = P.fy / v.fy;
+  const float rx = fx_rel / v.fx, ry = fy_rel / v.fy;
   const float ndr = P.n0 * rx + P.n1 * ry + P.n2;
   const bool ok = fabsf(ndr) >= 1e-8f && (1.f - P.T) >= 1e-6f;
   out.depth[q] = ok ? P.D / ndr : 0.f;
@@ -136,27 +146,28 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
   const int ty = lt / v.tiles_x, tx = lt - ty * v.tiles_x;
   int px, py0;
   warp_block_pixel<TW>(tx, ty, TH, px, py0);
-  const float fx_rel = (float)px + 0.5f - v.cx;
+  const int bx = block_origin(tx * TW), by = block_origin(ty * TH);
+  const float ox = __fsub_rn((float)bx, v.cx), oy = __fsub_rn((float)by, v.cy);
+  const float fxl = (float)(px - bx) + 0.5f, fyl0 = (float)(py0 - by) + 0.5f, fyl1 = fyl0 + 1.f;
   const uint2 rg = ranges[tile];
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max, t_min = b.p.t_min;
-  PixF P0{(float)py0 + 0.5f - v.cy, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 < v.H)};
-  PixF P1{(float)(py0 + 1) + 0.5f - v.cy, 1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y,
-          !(px < v.W && py0 + 1 < v.H)};
+  PixF P0{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 < v.H)};
+  PixF P1{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 + 1 < v.H)};
   for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
     if (__syncthreads_count(!(P0.done && P1.done)) == 0) break;
     const uint32_t j0 = start + threadIdx.x, j1 = j0 + NT;
-    if (j0 < rg.y) stage_record(s, threadIdx.x, rec, pair_g[j0], a_min);
-    if (j1 < rg.y) stage_record(s, threadIdx.x + NT, rec, pair_g[j1], a_min);
+    if (j0 < rg.y) stage_record(s, threadIdx.x, rec, pair_g[j0], a_min, ox, oy);
+    if (j1 < rg.y) stage_record(s, threadIdx.x + NT, rec, pair_g[j1], a_min, ox, oy);
     __syncthreads();
     const int cnt = min((uint32_t)kBatch, rg.y - start);
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, P0.done && P1.done)) break;
       const float4 q = s.q[k];
-      const float4 m = s.m[k];
+      const float2 m = s.m[k];
       const float p_lo = s.n[k].w;
-      const float dx = rel_d(fx_rel, m.x, m.z);
-      const float pw0 = eval_power(q, dx, rel_d(P0.fy, m.y, m.w));
-      const float pw1 = eval_power(q, dx, rel_d(P1.fy, m.y, m.w));
+      const float dx = __fsub_rn(fxl, m.x);
+      const float pw0 = eval_power(q, dx, __fsub_rn(fyl0, m.y));
+      const float pw1 = eval_power(q, dx, __fsub_rn(fyl1, m.y));
       // skip power > 0 and alpha < alpha_min (taken on the exponent); the warp skips a record none of its pixels takes
       const bool t0 = !P0.done && !(pw0 > 0.f) && pw0 >= p_lo;
       const bool t1 = !P1.done && !(pw1 > 0.f) && pw1 >= p_lo;
@@ -167,8 +178,8 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
       fwd_take(P1, t1, pw1, q.w, c, nn, j, a_max, t_min);
     }
   }
-  fwd_write(P0, v, b.p, px, py0, fx_rel, rg.x, out);
-  fwd_write(P1, v, b.p, px, py0 + 1, fx_rel, rg.x, out);
+  fwd_write(P0, v, b.p, px, py0, rg.x, out);
+  fwd_write(P1, v, b.p, px, py0 + 1, rg.x, out);
 }
 
 struct PixB {            // backward state of one pixel
@@ -243,7 +254,7 @@ constexpr int kTilePix = 256;
 struct BwdTab {                  // per pixel of the tile, in pixel order
   float4 g0[kTilePix];           // dL/dC (3), dL/dD
   float4 g1[kTilePix];           // dL/dN (3), last contributor + 1 (bits)
-  float2 f[kTilePix];            // pixel centre relative to the principal point
+  float2 f[kTilePix];            // pixel centre relative to the block origin
   float2 st[kTilePix];           // running (T, GS)
   uint8_t live[kTilePix];        // pixels still live in the current chunk
 };
@@ -263,6 +274,8 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
   const int lt = tile - v.tile_base;
   const int ty = lt / v.tiles_x, tx = lt - ty * v.tiles_x;
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max;
+  const int bx = block_origin(tx * TW), by = block_origin(ty * TH);
+  const float ox = __fsub_rn((float)bx, v.cx), oy = __fsub_rn((float)by, v.cy);
   uint32_t end = 0;
   for (int p = lane; p < kTilePix; p += 32) {
     const int px = tx * TW + p % TW, py = ty * TH + p / TW;
@@ -271,14 +284,19 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
     bwd_setup(P, v, b.p, px, py, fx, img, gi);
     tab.g0[p] = make_float4(P.gC0, P.gC1, P.gC2, P.gD);
     tab.g1[p] = make_float4(P.gN0, P.gN1, P.gN2, __uint_as_float(P.last));
-    tab.f[p] = make_float2(fx, P.fy);
+    tab.f[p] = make_float2((float)(px - bx) + 0.5f, (float)(py - by) + 0.5f);
     tab.st[p] = make_float2(P.T, P.GS);
     end = max(end, P.last);
   }
   end = min(__reduce_max_sync(FULL, end), rg.y);   // a stale `last` never walks past the tile's list
   for (uint32_t cend = end; cend > rg.x;) {
     const uint32_t cbase = cend > rg.x + 32 ? cend - 32 : rg.x;
-    const int top = (int)(cend - cbase) - 1;   // lane of the chunk's last record
+    const int n_rec = (int)(cend - cbase);
+    // A short chunk is replicated into 2 or 4 lane groups that take separate
+    // slices of the live pixels; their sums are combined before the atomics.
+    const int gsz = n_rec <= 8 ? 8 : (n_rec <= 16 ? 16 : 32);
+    const int lig = lane & (gsz - 1), grp = lane / gsz;
+    const int top = n_rec - 1;                 // lane (in its group) of the chunk's last record
     __syncwarp();
     int n_live = 0;
 #pragma unroll
@@ -288,38 +306,43 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
       if (lv) tab.live[n_live + __popc(m & ((1u << lane) - 1u))] = (uint8_t)(p0 + lane);
       n_live += __popc(m);
     }
-    const uint32_t j = cbase + lane;
-    const bool has = lane <= top;
+    const int ng = 32 / gsz;
+    const int seg = (n_live + ng - 1) / ng;
+    const int seg_lo = grp * seg, seg_hi = min(n_live, seg_lo + seg);
+    const uint32_t j = cbase + lig;
+    const bool has = lig <= top;
     uint32_t gid = 0;
     RecF r{};
     if (has) {
       gid = pair_g[j];
       r = load_record(rec, gid, a_min);
     }
+    const float2 mt = tile_mean(r.m, ox, oy);
     float acc[kGradFields];
 #pragma unroll
     for (int f = 0; f < kGradFields; ++f) acc[f] = 0.f;
     __syncwarp();
     float T = 0.f, GS = 0.f;
-    const int nsteps = n_live + top;
+    const int nsteps = seg + top;
     // Branch-free step: every lane evaluates its pair and masks what it does
     // not take, so consecutive steps can overlap (only T and GS are carried).
 #pragma unroll 2
     for (int s = 0; s < nsteps; ++s) {
-      const int pi = s - top + lane;
-      const bool act = has && (unsigned)pi < (unsigned)n_live;
+      const int q = s - top + lig;             // position in this group's slice
+      const int pi = seg_lo + q;
+      const bool act = has && q >= 0 && pi < seg_hi;
       const int pix = tab.live[act ? pi : 0];
       const float4 g1 = tab.g1[pix];
       const float2 f = tab.f[pix];
       const float4 g0 = tab.g0[pix];
       float Tin = __shfl_down_sync(FULL, T, 1);
       float GSin = __shfl_down_sync(FULL, GS, 1);
-      if (lane == top) {
+      if (lig == top) {
         const float2 t = tab.st[pix];
         Tin = t.x;
         GSin = t.y;
       }
-      const float dx = rel_d(f.x, r.m.x, r.m.z), dy = rel_d(f.y, r.m.y, r.m.w);
+      const float dx = __fsub_rn(f.x, mt.x), dy = __fsub_rn(f.y, mt.y);
       const float power = eval_power(r.q, dx, dy);
       const bool take = act && j < __float_as_uint(g1.w) && !(power > 0.f) && power >= r.n.w;
       const float a_raw = __fmul_rn(r.q.w, ex2_approx(power));
@@ -343,9 +366,13 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
       acc[3] = fmaf(G, dx * dy, acc[3]);
       acc[4] = fmaf(G, dy * dy, acc[4]);
       acc[5] += G;
-      if (act && lane == 0) tab.st[pix] = make_float2(T, GS);
+      if (act && lig == 0) tab.st[pix] = make_float2(T, GS);
     }
-    if (has) {
+    for (int off = 16; off >= gsz; off >>= 1) {
+#pragma unroll
+      for (int f = 0; f < kGradFields; ++f) acc[f] += __shfl_xor_sync(FULL, acc[f], off);
+    }
+    if (has && grp == 0) {
       float a[kGradFields];
       finish_grads(acc, r.q, a);
       float4* dst = reinterpret_cast<float4*>(grad + (size_t)gid * 16);
