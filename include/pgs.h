@@ -284,7 +284,7 @@ pgs_status pgs_exclusive_scan_u32(const uint32_t* d_in, const uint32_t* d_index,
  * 0 <= n <= 1048576) key/value pairs in place on bits [bit_lo, bit_hi), with
  * the same stable order as pgs_sort_pairs.  All scratch (histograms,
  * look-back status, ping-pong keys and values) sits in one fixed array of
- * about 8.9 MB inside the library's device image, which every GPU that loads
+ * about 9.4 MB inside the library's device image, which every GPU that loads
  * the library holds until the process exits; nothing is allocated or freed.
  * The first call on a device looks up that array's device address (make it
  * before any stream capture).  Every call on a device shares the array and it

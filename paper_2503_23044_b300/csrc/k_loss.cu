@@ -33,17 +33,41 @@ __device__ __forceinline__ PixCtx pix_ctx(const BatchDev& b, long long p, int& v
   return c;
 }
 
-// depth-derived normal at an interior pixel; false when not valid
-__device__ __forceinline__ bool depth_normal(const BatchDev& b, const PixCtx& c, const float* __restrict__ depth,
-                                             float nd[3]) {
-  const ViewDev& v = b.v[c.v];
-  if (c.px < 1 || c.py < 1 || c.px > v.W - 2 || c.py > v.H - 2) return false;
-  const long long p = c.p;
-  const float d0 = depth[p], dl = depth[p - 1], dr = depth[p + 1], du = depth[p - v.W], dd = depth[p + v.W];
-  if (!(d0 > 0.f && dl > 0.f && dr > 0.f && du > 0.f && dd > 0.f)) return false;
+// Inputs of one pixel, loaded before any arithmetic so that a thread keeps
+// the loads of several pixels in flight (the loss is bound by HBM traffic).
+struct PixIn {
+  PixCtx c;
+  bool inter;                 // interior pixel (the 5-point stencil exists)
+  float d0, dl, dr, du, dd;   // D_hat at the pixel and its 4 neighbours
+  float N[3];                 // N_hat
+  float mask;
+};
+
+__device__ __forceinline__ void load_pix(const BatchDev& b, long long p, int& vh, const float* __restrict__ depth,
+                                         const float* __restrict__ normal, const float* __restrict__ mask,
+                                         PixIn& I) {
+  I.c = pix_ctx(b, p, vh);
+  const ViewDev& v = b.v[I.c.v];
+  I.inter = I.c.px >= 1 && I.c.py >= 1 && I.c.px <= v.W - 2 && I.c.py <= v.H - 2;
+  I.d0 = __ldg(depth + p);
+  I.dl = I.dr = I.du = I.dd = 0.f;
+  if (I.inter) {
+    I.dl = __ldg(depth + p - 1); I.dr = __ldg(depth + p + 1);
+    I.du = __ldg(depth + p - v.W); I.dd = __ldg(depth + p + v.W);
+  }
+  I.N[0] = __ldg(normal + I.c.p3); I.N[1] = __ldg(normal + I.c.p3 + I.c.HW); I.N[2] = __ldg(normal + I.c.p3 + 2 * I.c.HW);
+  I.mask = __ldg(mask + p);
+}
+
+// depth-derived normal N_d (stop-gradient) and |N_hat|; false when the pixel is not valid
+__device__ __forceinline__ bool normal_valid(const BatchDev& b, const PixIn& I, float nd[3], float& nn) {
+  if (!I.inter) return false;
+  if (!(I.d0 > 0.f && I.dl > 0.f && I.dr > 0.f && I.du > 0.f && I.dd > 0.f)) return false;
+  const ViewDev& v = b.v[I.c.v];
   const float ifx = 1.f / v.fx, ify = 1.f / v.fy;
-  const float u = (float)c.px + 0.5f - v.cx, w = (float)c.py + 0.5f - v.cy;
-  // P = D_hat * ((u - cx)/fx, (v - cy)/fy, 1)
+  const float u = (float)I.c.px + 0.5f - v.cx, w = (float)I.c.py + 0.5f - v.cy;
+  // P = D_hat * ((u - cx)/fx, (v - cy)/fy, 1); N_d = normalised (dP/du x dP/dv), facing the camera
+  const float dl = I.dl, dr = I.dr, du = I.du, dd = I.dd;
   const float ex0 = dr * (u + 1.f) * ifx - dl * (u - 1.f) * ifx, ex1 = (dr - dl) * w * ify, ex2 = dr - dl;
   const float ey0 = (dd - du) * u * ifx, ey1 = dd * (w + 1.f) * ify - du * (w - 1.f) * ify, ey2 = dd - du;
   float c0 = ex1 * ey2 - ex2 * ey1, c1 = ex2 * ey0 - ex0 * ey2, c2 = ex0 * ey1 - ex1 * ey0;
@@ -51,17 +75,10 @@ __device__ __forceinline__ bool depth_normal(const BatchDev& b, const PixCtx& c,
   if (!(nrm > 1e-20f)) return false;
   const float in = 1.f / nrm;
   c0 *= in; c1 *= in; c2 *= in;
-  const float face = c0 * d0 * u * ifx + c1 * d0 * w * ify + c2 * d0;
+  const float face = c0 * I.d0 * u * ifx + c1 * I.d0 * w * ify + c2 * I.d0;
   if (face > 0.f) { c0 = -c0; c1 = -c1; c2 = -c2; }
   nd[0] = c0; nd[1] = c1; nd[2] = c2;
-  return true;
-}
-
-__device__ __forceinline__ bool normal_valid(const BatchDev& b, const PixCtx& c, const pgs_image_ptrs& img, float nd[3],
-                                             float N[3], float& nn) {
-  if (!depth_normal(b, c, img.depth, nd)) return false;
-  N[0] = img.normal[c.p3]; N[1] = img.normal[c.p3 + c.HW]; N[2] = img.normal[c.p3 + 2 * c.HW];
-  nn = sqrtf(N[0] * N[0] + N[1] * N[1] + N[2] * N[2]);
+  nn = sqrtf(I.N[0] * I.N[0] + I.N[1] * I.N[1] + I.N[2] * I.N[2]);
   return nn > 1e-8f;
 }
 
@@ -71,19 +88,35 @@ __device__ __forceinline__ void range_of_block(long long n, long long& s, long l
   e = min(n, s + per);
 }
 
+constexpr int kCountUnroll = 4;  // pixels per thread per iteration, loads first
+constexpr int kGradUnroll = 2;
+
 __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
                                                      pgs_target_ptrs tgt, uint32_t* __restrict__ counts) {
   __shared__ uint32_t s_cnt[kMaxViews][2];
   for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
   __syncthreads();
+  const float* __restrict__ depth = img.depth;
+  const float* __restrict__ normal = img.normal;
+  const float* __restrict__ mask = tgt.mask;
   long long s, e;
   range_of_block(b.total_pixels, s, e);
   int vh = s < e ? view_of_pixel(b, s) : 0;
-  for (long long p = s + threadIdx.x; p < e; p += blockDim.x) {
-    const PixCtx c = pix_ctx(b, p, vh);
-    float nd[3], N[3], nn;
-    if (tgt.mask[p] > 0.f) atomicAdd(&s_cnt[c.v][0], 1u);
-    if (normal_valid(b, c, img, nd, N, nn)) atomicAdd(&s_cnt[c.v][1], 1u);
+  for (long long p0 = s + threadIdx.x; p0 < e; p0 += kCountUnroll * (long long)blockDim.x) {
+    PixIn I[kCountUnroll];
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const long long p = p0 + u * (long long)blockDim.x;
+      if (p < e) load_pix(b, p, vh, depth, normal, mask, I[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < kCountUnroll; ++u) {
+      const long long p = p0 + u * (long long)blockDim.x;
+      if (p >= e) break;
+      float nd[3], nn;
+      if (I[u].mask > 0.f) atomicAdd(&s_cnt[I[u].c.v][0], 1u);
+      if (normal_valid(b, I[u], nd, nn)) atomicAdd(&s_cnt[I[u].c.v][1], 1u);
+    }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x)
@@ -92,51 +125,78 @@ __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ Bat
 
 __device__ __forceinline__ float sgnf(float x) { return (float)((x > 0.f) - (x < 0.f)); }
 
-__global__ void __launch_bounds__(256) k_loss_grad(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
+__global__ void __launch_bounds__(256, 3) k_loss_grad(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
                                                    pgs_target_ptrs tgt, pgs_loss_params lp,
                                                    const uint32_t* __restrict__ counts, pgs_image_grad_ptrs g,
                                                    float* __restrict__ partials, uint32_t* err) {
   __shared__ float s_red[3][256];
+  const float* __restrict__ depth = img.depth;
+  const float* __restrict__ normal = img.normal;
+  const float* __restrict__ rgb = img.rgb;
+  const float* __restrict__ trgb = tgt.rgb;
+  const float* __restrict__ prior = tgt.prior;
+  const float* __restrict__ mask = tgt.mask;
+  float* __restrict__ g_rgb = g.rgb;
+  float* __restrict__ g_depth = g.depth;
+  float* __restrict__ g_normal = g.normal;
   long long s, e;
   range_of_block(b.total_pixels, s, e);
   const float invB = 1.f / (float)b.n_views;
   float l_rgb = 0.f, l_d = 0.f, l_n = 0.f;
   bool bad = false;
   int vh = s < e ? view_of_pixel(b, s) : 0;
-  for (long long p = s + threadIdx.x; p < e; p += blockDim.x) {
-    const PixCtx c = pix_ctx(b, p, vh);
-    const float k_rgb = invB / (3.f * (float)c.HW);
+  for (long long p0 = s + threadIdx.x; p0 < e; p0 += kGradUnroll * (long long)blockDim.x) {
+    PixIn I[kGradUnroll];
+    float c3[kGradUnroll][3], t3[kGradUnroll][3], pr[kGradUnroll];
 #pragma unroll
-    for (int ch = 0; ch < 3; ++ch) {
-      const long long q = c.p3 + ch * c.HW;
-      const float d = img.rgb[q] - tgt.rgb[q];
-      l_rgb += fabsf(d) * k_rgb;
-      g.rgb[q] = sgnf(d) * k_rgb;
+    for (int u = 0; u < kGradUnroll; ++u) {
+      const long long p = p0 + u * (long long)blockDim.x;
+      if (p < e) {
+        load_pix(b, p, vh, depth, normal, mask, I[u]);
+#pragma unroll
+        for (int ch = 0; ch < 3; ++ch) {
+          c3[u][ch] = __ldg(rgb + I[u].c.p3 + ch * I[u].c.HW);
+          t3[u][ch] = __ldg(trgb + I[u].c.p3 + ch * I[u].c.HW);
+        }
+        pr[u] = __ldg(prior + p);
+      }
     }
-    const float mask = tgt.mask[p];
-    float gd = 0.f;
-    if (mask > 0.f) {
-      const float kd = lp.lambda_depth * invB / fmaxf(1.f, (float)counts[2 * c.v]);
-      const float d = img.depth[p] - tgt.prior[p];
-      l_d += mask * fabsf(d) * kd;
-      gd = mask * sgnf(d) * kd;
+#pragma unroll
+    for (int u = 0; u < kGradUnroll; ++u) {
+      const long long p = p0 + u * (long long)blockDim.x;
+      if (p >= e) break;
+      const PixIn& P = I[u];
+      const float k_rgb = invB / (3.f * (float)P.c.HW);
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float d = c3[u][ch] - t3[u][ch];
+        l_rgb += fabsf(d) * k_rgb;
+        g_rgb[P.c.p3 + ch * P.c.HW] = sgnf(d) * k_rgb;
+      }
+      float gd = 0.f;
+      if (P.mask > 0.f) {
+        const float kd = lp.lambda_depth * invB / fmaxf(1.f, (float)counts[2 * P.c.v]);
+        const float d = P.d0 - pr[u];
+        l_d += P.mask * fabsf(d) * kd;
+        gd = P.mask * sgnf(d) * kd;
+      }
+      g_depth[p] = gd;
+      float nd[3], nn, gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
+      if (normal_valid(b, P, nd, nn)) {
+        const float kn = lp.lambda_normal * invB / fmaxf(1.f, (float)counts[2 * P.c.v + 1]);
+        const float inn = 1.f / nn;
+        const float cosang = (nd[0] * P.N[0] + nd[1] * P.N[1] + nd[2] * P.N[2]) * inn;
+        l_n += (1.f - cosang) * kn;
+        // d/dN of -(N_d . N)/|N| = -(N_d/|N| - cos N/|N|^2)
+        gn0 = -kn * (nd[0] * inn - cosang * P.N[0] * inn * inn);
+        gn1 = -kn * (nd[1] * inn - cosang * P.N[1] * inn * inn);
+        gn2 = -kn * (nd[2] * inn - cosang * P.N[2] * inn * inn);
+      }
+      g_normal[P.c.p3] = gn0;
+      g_normal[P.c.p3 + P.c.HW] = gn1;
+      g_normal[P.c.p3 + 2 * P.c.HW] = gn2;
+      bad |= !isfinite(gd) || !isfinite(gn0) || !isfinite(gn1) || !isfinite(gn2);
     }
-    g.depth[p] = gd;
-    float nd[3], N[3], nn, gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
-    if (normal_valid(b, c, img, nd, N, nn)) {
-      const float kn = lp.lambda_normal * invB / fmaxf(1.f, (float)counts[2 * c.v + 1]);
-      const float inn = 1.f / nn;
-      const float cosang = (nd[0] * N[0] + nd[1] * N[1] + nd[2] * N[2]) * inn;
-      l_n += (1.f - cosang) * kn;
-      // d/dN of -(N_d . N)/|N| = -(N_d/|N| - cos N/|N|^2)
-      gn0 = -kn * (nd[0] * inn - cosang * N[0] * inn * inn);
-      gn1 = -kn * (nd[1] * inn - cosang * N[1] * inn * inn);
-      gn2 = -kn * (nd[2] * inn - cosang * N[2] * inn * inn);
-    }
-    g.normal[c.p3] = gn0;
-    g.normal[c.p3 + c.HW] = gn1;
-    g.normal[c.p3 + 2 * c.HW] = gn2;
-    bad |= !isfinite(gd) || !isfinite(gn0) || !isfinite(gn1) || !isfinite(gn2);
   }
   if (bad) set_flag(err, kFlagNonfinite);
   s_red[0][threadIdx.x] = l_rgb;

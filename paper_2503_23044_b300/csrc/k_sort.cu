@@ -6,7 +6,7 @@
 // tiles are emitted in depth order and the pairs are stably sorted by tile id
 // only.  Both stages use the same onesweep pass (global digit histogram once,
 // then one pass per 8-bit digit with a decoupled look-back across tiles of
-// 4096 keys).  Every spin in the look-back is bounded: past the limit the pass
+// 2048 keys).  Every spin in the look-back is bounded: past the limit the pass
 // raises PGS_ERR_TIMEOUT and carries on, so no launch can hang.
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
@@ -123,8 +123,9 @@ void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* 
 // ------------------------------------------------------------------ onesweep radix sort
 constexpr int kSortThreads = 256;
 constexpr int kSortWarps = kSortThreads / 32;
-constexpr int kSortItems = 16;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
+constexpr int kSortItems = 8;
+constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
+static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch layout");
 constexpr int kRadix = 256;
 constexpr uint32_t kStFlagAgg = 1u << 30, kStFlagInc = 2u << 30, kStMask = (1u << 30) - 1;
 
@@ -151,7 +152,7 @@ SortScratch sort_scratch_layout(void* base, long long n_max) {
   s.err = s.counters + 4;                                   // [1] (+3 pad)
   s.max_tiles = (n_max + kSortTile - 1) / kSortTile + 1;
   s.status = s.err + 4;                                     // [2][max_tiles][256]
-  s.bytes = (size_t)(4 * kRadix + 8) * 4 + (size_t)2 * s.max_tiles * kRadix * 4;
+  s.bytes = sort_scratch_bytes_for(n_max);
   return s;
 }
 
@@ -190,7 +191,7 @@ __global__ void __launch_bounds__(kRadix) k_sort_hist_scan(uint32_t* __restrict_
   }
 }
 
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const long long* __restrict__ d_n, long long n_max, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
@@ -248,23 +249,35 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(
     unsigned long long tot;
     const uint32_t excl = (uint32_t)block_exclusive_scan_u64(run, s_w, tot);
     s_excl[d] = excl;
-    // decoupled look-back over earlier tiles, bounded
+    // decoupled look-back over earlier tiles, eight status words per round
+    // (independent loads), each wait bounded
     uint32_t prefix = 0;
     if (tile > 0) {
       long long j = tile - 1;
       uint32_t spins = 0;
-      while (j >= 0) {
-        const uint32_t w = ld_relaxed(status + j * kRadix + d);
-        const uint32_t f = w & ~kStMask;
-        if (f == 0u) {
-          if (++spins > spin_limit) { atomicOr(err, kFlagTimeout); break; }
-          if ((spins & 255u) == 0u && (ld_relaxed(err) & kFlagTimeout)) break;
-          __nanosleep(32);
-          continue;
+      bool stop = false;
+      while (!stop && j >= 0) {
+        constexpr int kLB = 8;
+        uint32_t w[kLB];
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) w[k] = (j - k >= 0) ? ld_relaxed(status + (j - k) * kRadix + d) : kStFlagInc;
+#pragma unroll
+        for (int k = 0; k < kLB; ++k) {
+          if (stop) break;
+          uint32_t f = w[k] & ~kStMask;
+          while (f == 0u) {          // tile j - k has not published yet
+            if (++spins > spin_limit) { atomicOr(err, kFlagTimeout); break; }
+            if ((spins & 255u) == 0u && (ld_relaxed(err) & kFlagTimeout)) break;
+            __nanosleep(32);
+            w[k] = ld_relaxed(status + (j - k) * kRadix + d);
+            f = w[k] & ~kStMask;
+          }
+          if (f == 0u) { stop = true; break; }   // gave up (timeout flagged)
+          if (j - k < 0) { stop = true; break; }  // ran past tile 0
+          prefix += w[k] & kStMask;
+          if (f == kStFlagInc) stop = true;
         }
-        prefix += w & kStMask;
-        if (f == kStFlagInc) break;
-        --j;
+        j -= kLB;
       }
       st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
     }
@@ -318,9 +331,18 @@ cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
   uint32_t* status[2] = {s.status, s.status + (size_t)s.max_tiles * kRadix};
   k_sort_hist<<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0]);
   k_sort_hist_scan<<<1, kRadix, 0, st>>>(s.hist, np);
+  // persistent passes: one resident wave (tiles are taken from a counter)
+  static int per_sm = -1;
+  if (per_sm < 0) {
+    cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_pass, kSortThreads, 0) != cudaSuccess ||
+        per_sm < 1)
+      per_sm = 1;
+  }
+  const int pass_grid = (int)std::max(1ll, std::min((long long)per_sm * num_sms, (n_max + kSortTile - 1) / kSortTile));
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int p = 0; p < np; ++p) {
-    k_sort_pass<<<num_sms * 2, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + 8 * p,
+    k_sort_pass<<<pass_grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + 8 * p,
                                                      digit_mask(bit_lo + 8 * p, bit_hi), s.hist + p * kRadix,
                                                      s.counters + p, status[p & 1],
                                                      p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit);

@@ -43,6 +43,12 @@ __global__ void k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anch
 // k_sort.cu
 void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
                            const long long* d_n, unsigned long long* sums, cudaStream_t st);
+// keys per onesweep tile; the scratch layout below holds two look-back status
+// arrays of (n_max / kSortTileKeys + 1) x 256 words after the histograms
+constexpr int kSortTileKeys = 2048;
+constexpr size_t sort_scratch_bytes_for(long long n_max) {
+  return (size_t)(4 * 256 + 8) * 4 + (size_t)2 * ((n_max + kSortTileKeys - 1) / kSortTileKeys + 1) * 256 * 4;
+}
 SortScratch sort_scratch_layout(void* base, long long n_max);
 int sort_passes(int bit_lo, int bit_hi);
 cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,

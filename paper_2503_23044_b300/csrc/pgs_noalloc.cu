@@ -12,7 +12,7 @@
 //
 // The array holds the device copy of n, the digit histograms, the look-back
 // status words and the ping-pong keys/values for at most kNoAllocMaxN pairs,
-// about 8.9 MB; every GPU that loads the library keeps it until the process
+// about 9.4 MB; every GPU that loads the library keeps it until the process
 // exits.  Host code cannot use the array's name as a device address, so the
 // address is looked up once per device with cudaGetSymbolAddress.
 #include <cstdio>
@@ -25,7 +25,7 @@ namespace {
 
 constexpr long long kNoAllocMaxN = 1ll << 20;
 constexpr size_t kNoAllocHeader = 256;   // n (int64) + error word, padded
-constexpr size_t kNoAllocSortBytes = (size_t)(4 * 256 + 8) * 4 + (size_t)2 * ((kNoAllocMaxN + 4095) / 4096 + 1) * 256 * 4;
+constexpr size_t kNoAllocSortBytes = pgs::sort_scratch_bytes_for(kNoAllocMaxN);
 constexpr size_t kNoAllocPing = (size_t)kNoAllocMaxN * 4;
 constexpr size_t kNoAllocBytes =
     kNoAllocHeader + ((kNoAllocSortBytes + 255) / 256) * 256 + 2 * kNoAllocPing;
