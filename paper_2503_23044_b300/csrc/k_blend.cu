@@ -259,6 +259,68 @@ struct BwdTab {                  // per pixel of the tile, in pixel order
   uint8_t live[kTilePix];        // pixels still live in the current chunk
 };
 
+// One record of a lane against the pixel passing through it: undo the
+// record's contribution to the pixel's transmittance (T_i = T_{i+1} / (1 - alpha_i)),
+// carry GS, and add the pixel's terms to the record's sums.  Branch-free: a
+// pair that the forward did not take leaves T, GS and the sums unchanged.
+__device__ __forceinline__ void bwd_pair(const RecF& r, float2 mt, uint32_t j, bool act, const float4 g0,
+                                         const float4 g1, const float2 f, float& T, float& GS,
+                                         float acc[kGradFields], float a_max) {
+  const float dx = __fsub_rn(f.x, mt.x), dy = __fsub_rn(f.y, mt.y);
+  const float power = eval_power(r.q, dx, dy);
+  const bool take = act && j < __float_as_uint(g1.w) && !(power > 0.f) && power >= r.n.w;
+  const float a_raw = __fmul_rn(r.q.w, ex2_approx(power));
+  const float alpha = fminf(a_max, a_raw);
+  const float iom = rcp_approx(__fsub_rn(1.f, alpha));
+  const float Tin = T, GSin = GS;
+  T = take ? Tin * iom : Tin;
+  const float w = take ? alpha * T : 0.f;
+  float gf = g0.x * r.c.x;
+  gf = fmaf(g0.y, r.c.y, gf); gf = fmaf(g0.z, r.c.z, gf); gf = fmaf(g0.w, r.c.w, gf);
+  gf = fmaf(g1.x, r.n.x, gf); gf = fmaf(g1.y, r.n.y, gf); gf = fmaf(g1.z, r.n.z, gf);
+  const float dLda = fmaf(T, gf, -GSin * iom);
+  GS = fmaf(w, gf, GSin);
+  acc[6] = fmaf(w, g0.x, acc[6]); acc[7] = fmaf(w, g0.y, acc[7]); acc[8] = fmaf(w, g0.z, acc[8]);
+  acc[9] = fmaf(w, g0.w, acc[9]);
+  acc[10] = fmaf(w, g1.x, acc[10]); acc[11] = fmaf(w, g1.y, acc[11]); acc[12] = fmaf(w, g1.z, acc[12]);
+  // alpha clamped at alpha_max carries no gradient to o, mean, conic
+  const float G = (take && !(a_raw > a_max)) ? dLda * a_raw : 0.f;
+  acc[0] = fmaf(G, dx, acc[0]);
+  acc[1] = fmaf(G, dy, acc[1]);
+  acc[2] = fmaf(G, dx * dx, acc[2]);
+  acc[3] = fmaf(G, dx * dy, acc[3]);
+  acc[4] = fmaf(G, dy * dy, acc[4]);
+  acc[5] += G;
+}
+
+// add one record's per-tile sums to its gradient row (nonzero float4 parts only)
+__device__ __forceinline__ void flush_record(const float acc[kGradFields], float4 q, uint32_t gid,
+                                             float* __restrict__ grad) {
+  float a[kGradFields];
+  finish_grads(acc, q, a);
+  float4* dst = reinterpret_cast<float4*>(grad + (size_t)gid * 16);
+  const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
+  const float4 v1 = make_float4(a[4], a[5], a[6], a[7]);
+  const float4 v2 = make_float4(a[8], a[9], a[10], a[11]);
+  if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(dst, v0);
+  if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f || v1.w != 0.f) atomicAdd(dst + 1, v1);
+  if (v2.x != 0.f || v2.y != 0.f || v2.z != 0.f || v2.w != 0.f) atomicAdd(dst + 2, v2);
+  if (a[12] != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 3), a[12]);
+}
+
+// pixels with a contributor at or below index cbase, listed in pixel order; returns their number
+__device__ __forceinline__ int build_live(BwdTab& tab, uint32_t cbase, int lane) {
+  int n_live = 0;
+#pragma unroll
+  for (int p0 = 0; p0 < kTilePix; p0 += 32) {
+    const bool lv = __float_as_uint(tab.g1[p0 + lane].w) > cbase;
+    const unsigned m = __ballot_sync(0xffffffffu, lv);
+    if (lv) tab.live[n_live + __popc(m & ((1u << lane) - 1u))] = (uint8_t)(p0 + lane);
+    n_live += __popc(m);
+  }
+  return n_live;
+}
+
 template <int TW>
 __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdTab& tab,
                                                const float4* __restrict__ rec, const uint32_t* __restrict__ pair_g,
@@ -290,22 +352,63 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
   }
   end = min(__reduce_max_sync(FULL, end), rg.y);   // a stale `last` never walks past the tile's list
   for (uint32_t cend = end; cend > rg.x;) {
-    const uint32_t cbase = cend > rg.x + 32 ? cend - 32 : rg.x;
-    const int n_rec = (int)(cend - cbase);
-    // A short chunk is replicated into 2 or 4 lane groups that take separate
-    // slices of the live pixels; their sums are combined before the atomics.
+    const uint32_t avail = cend - rg.x;
+    if (avail > 32) {
+      // Dual chunk of 33..64 records: lane l holds records B = cbase + l + min(l, n2)
+      // and, for l < n2, A = B + 1; a pixel meets A then B in each lane, so
+      // the per-step overhead (pixel loads, shuffles, state) serves two pairs.
+      const int n_rec = (int)min(avail, 64u);
+      const uint32_t cbase = cend - n_rec;
+      const int n2 = n_rec - 32;
+      __syncwarp();
+      const int n_live = build_live(tab, cbase, lane);
+      const uint32_t jB = cbase + lane + min(lane, n2), jA = jB + 1;
+      const bool hasA = lane < n2;
+      const uint32_t gB = pair_g[jB], gA = hasA ? pair_g[jA] : 0u;
+      const RecF rB = load_record(rec, gB, a_min);
+      RecF rA{};
+      if (hasA) rA = load_record(rec, gA, a_min);
+      const float2 mtB = tile_mean(rB.m, ox, oy), mtA = tile_mean(rA.m, ox, oy);
+      float accA[kGradFields], accB[kGradFields];
+#pragma unroll
+      for (int f = 0; f < kGradFields; ++f) accA[f] = accB[f] = 0.f;
+      __syncwarp();
+      float T = 0.f, GS = 0.f;
+      const int nsteps = n_live + 31;
+#pragma unroll 2
+      for (int s = 0; s < nsteps; ++s) {
+        const int pi = s - 31 + lane;
+        const bool act = (unsigned)pi < (unsigned)n_live;
+        const int pix = tab.live[act ? pi : 0];
+        const float4 g1 = tab.g1[pix];
+        const float2 f = tab.f[pix];
+        const float4 g0 = tab.g0[pix];
+        T = __shfl_down_sync(FULL, T, 1);
+        GS = __shfl_down_sync(FULL, GS, 1);
+        if (lane == 31) {
+          const float2 t = tab.st[pix];
+          T = t.x;
+          GS = t.y;
+        }
+        bwd_pair(rA, mtA, jA, act && hasA, g0, g1, f, T, GS, accA, a_max);
+        bwd_pair(rB, mtB, jB, act, g0, g1, f, T, GS, accB, a_max);
+        if (act && lane == 0) tab.st[pix] = make_float2(T, GS);
+      }
+      flush_record(accB, rB.q, gB, grad);
+      if (hasA) flush_record(accA, rA.q, gA, grad);
+      cend = cbase;
+      continue;
+    }
+    // Single chunk of up to 32 records (the tile's last): lane l holds record
+    // cbase + l.  A short chunk is replicated into 2 or 4 lane groups that take
+    // separate slices of the live pixels; their sums are combined before the atomics.
+    const uint32_t cbase = rg.x;
+    const int n_rec = (int)avail;
     const int gsz = n_rec <= 8 ? 8 : (n_rec <= 16 ? 16 : 32);
     const int lig = lane & (gsz - 1), grp = lane / gsz;
     const int top = n_rec - 1;                 // lane (in its group) of the chunk's last record
     __syncwarp();
-    int n_live = 0;
-#pragma unroll
-    for (int p0 = 0; p0 < kTilePix; p0 += 32) {
-      const bool lv = __float_as_uint(tab.g1[p0 + lane].w) > cbase;
-      const unsigned m = __ballot_sync(FULL, lv);
-      if (lv) tab.live[n_live + __popc(m & ((1u << lane) - 1u))] = (uint8_t)(p0 + lane);
-      n_live += __popc(m);
-    }
+    const int n_live = build_live(tab, cbase, lane);
     const int ng = 32 / gsz;
     const int seg = (n_live + ng - 1) / ng;
     const int seg_lo = grp * seg, seg_hi = min(n_live, seg_lo + seg);
@@ -324,8 +427,6 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
     __syncwarp();
     float T = 0.f, GS = 0.f;
     const int nsteps = seg + top;
-    // Branch-free step: every lane evaluates its pair and masks what it does
-    // not take, so consecutive steps can overlap (only T and GS are carried).
 #pragma unroll 2
     for (int s = 0; s < nsteps; ++s) {
       const int q = s - top + lig;             // position in this group's slice
@@ -335,58 +436,25 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
       const float4 g1 = tab.g1[pix];
       const float2 f = tab.f[pix];
       const float4 g0 = tab.g0[pix];
-      float Tin = __shfl_down_sync(FULL, T, 1);
-      float GSin = __shfl_down_sync(FULL, GS, 1);
+      T = __shfl_down_sync(FULL, T, 1);
+      GS = __shfl_down_sync(FULL, GS, 1);
       if (lig == top) {
         const float2 t = tab.st[pix];
-        Tin = t.x;
-        GSin = t.y;
+        T = t.x;
+        GS = t.y;
       }
-      const float dx = __fsub_rn(f.x, mt.x), dy = __fsub_rn(f.y, mt.y);
-      const float power = eval_power(r.q, dx, dy);
-      const bool take = act && j < __float_as_uint(g1.w) && !(power > 0.f) && power >= r.n.w;
-      const float a_raw = __fmul_rn(r.q.w, ex2_approx(power));
-      const float alpha = fminf(a_max, a_raw);
-      const float iom = rcp_approx(__fsub_rn(1.f, alpha));
-      T = take ? Tin * iom : Tin;
-      const float w = take ? alpha * T : 0.f;
-      float gf = g0.x * r.c.x;
-      gf = fmaf(g0.y, r.c.y, gf); gf = fmaf(g0.z, r.c.z, gf); gf = fmaf(g0.w, r.c.w, gf);
-      gf = fmaf(g1.x, r.n.x, gf); gf = fmaf(g1.y, r.n.y, gf); gf = fmaf(g1.z, r.n.z, gf);
-      const float dLda = fmaf(T, gf, -GSin * iom);
-      GS = fmaf(w, gf, GSin);
-      acc[6] = fmaf(w, g0.x, acc[6]); acc[7] = fmaf(w, g0.y, acc[7]); acc[8] = fmaf(w, g0.z, acc[8]);
-      acc[9] = fmaf(w, g0.w, acc[9]);
-      acc[10] = fmaf(w, g1.x, acc[10]); acc[11] = fmaf(w, g1.y, acc[11]); acc[12] = fmaf(w, g1.z, acc[12]);
-      // alpha clamped at alpha_max carries no gradient to o, mean, conic
-      const float G = (take && !(a_raw > a_max)) ? dLda * a_raw : 0.f;
-      acc[0] = fmaf(G, dx, acc[0]);
-      acc[1] = fmaf(G, dy, acc[1]);
-      acc[2] = fmaf(G, dx * dx, acc[2]);
-      acc[3] = fmaf(G, dx * dy, acc[3]);
-      acc[4] = fmaf(G, dy * dy, acc[4]);
-      acc[5] += G;
+      bwd_pair(r, mt, j, act, g0, g1, f, T, GS, acc, a_max);
       if (act && lig == 0) tab.st[pix] = make_float2(T, GS);
     }
     for (int off = 16; off >= gsz; off >>= 1) {
 #pragma unroll
       for (int f = 0; f < kGradFields; ++f) acc[f] += __shfl_xor_sync(FULL, acc[f], off);
     }
-    if (has && grp == 0) {
-      float a[kGradFields];
-      finish_grads(acc, r.q, a);
-      float4* dst = reinterpret_cast<float4*>(grad + (size_t)gid * 16);
-      const float4 v0 = make_float4(a[0], a[1], a[2], a[3]);
-      const float4 v1 = make_float4(a[4], a[5], a[6], a[7]);
-      const float4 v2 = make_float4(a[8], a[9], a[10], a[11]);
-      if (v0.x != 0.f || v0.y != 0.f || v0.z != 0.f || v0.w != 0.f) atomicAdd(dst, v0);
-      if (v1.x != 0.f || v1.y != 0.f || v1.z != 0.f || v1.w != 0.f) atomicAdd(dst + 1, v1);
-      if (v2.x != 0.f || v2.y != 0.f || v2.z != 0.f || v2.w != 0.f) atomicAdd(dst + 2, v2);
-      if (a[12] != 0.f) atomicAdd(reinterpret_cast<float*>(dst + 3), a[12]);
-    }
+    if (has && grp == 0) flush_record(acc, r.q, gid, grad);
     cend = cbase;
   }
 }
+
 // Persistent kernels: one resident wave of CTAs takes tiles from a global queue
 // in the given order (longest lists first), so long tiles do not form a tail.
 template <int TW, int TH>
