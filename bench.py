@@ -108,6 +108,12 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------ workload
+def resolution_desc(cams) -> str:
+    from collections import Counter
+    cnt = Counter(f"{c.width}x{c.height}" for c in cams)
+    return ", ".join(k if n == 1 else f"{n}x {k}" for k, n in cnt.items())
+
+
 def make_workload(name: str, seed: int, device: str):
     from paper_2503_23044_b300 import synth
     sc = synth.anchor_scene(name, seed=seed)
@@ -184,13 +190,14 @@ def run_reference(args):
     timed = per_step[args.warmup:]
     value = len(timed) / sum(timed)
     cores = torch.get_num_threads()
-    sample = (f"per step one of the {V} 1600x1064 views: FP64 decode+projection of every LoD-active anchor, then a "
+    sample = (f"per step one of the {V} views ({resolution_desc(sc['cameras'])}): FP64 decode+projection of every "
+              "LoD-active anchor, then a "
               "64x64 crop fwd+bwd; per-pixel cost extrapolated to the full frame")
     line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * sum(timed) / len(timed), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
                 config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
-                            resolution="1600x1064", l2="n/a (CPU)"),
+                            resolution=resolution_desc(sc["cameras"]), l2="n/a (CPU)"),
                 cpu_baseline=dict(value=value, unit="views/s", cores=cores, kind="oracle", sample=sample),
                 e2e=dict(value=value, unit="views/s", h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line), flush=True)
@@ -213,6 +220,7 @@ def run_pgs(args):
     cams = sc["cameras"]
     V = len(cams)
     packed = B.pack_cameras(cams)
+    res_desc = resolution_desc(cams)
     precision = B.DECODE_BF16 if args.decode == "bf16" else B.DECODE_FP32
     scene, t, pg = build_scene(sc, B, device, args.cap_pairs, args.cap_rows, precision)
     targets = B.Targets.from_views(tviews, device=device)
@@ -241,6 +249,15 @@ def run_pgs(args):
     scene.read_status(stream)
     n_eval = float(images.n_eval.double().sum())
     n_contrib = float(images.n_contrib.double().sum())
+
+    # launch-shape autotuner (tile shape x shared-memory batch), outside the timed region
+    tune = []
+    if not args.no_tune:
+        with torch.cuda.stream(stream):
+            tune = scene.autotune(cams, images, grads, pg, reps=3, stream=stream, packed=packed)
+        scene.read_status(stream)
+    tp = scene.params()
+    tile_desc = f"{tp['tile_w']}x{tp['tile_h']}"
 
     # capture the whole step in one CUDA graph, with the stage events inside it
     scene.set_profiling(True)
@@ -394,9 +411,12 @@ def run_pgs(args):
                     ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
                     config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
-                                resolution="1600x1064", form="batched: all views per call, CUDA graph" if use_graph
+                                resolution=res_desc, form="batched: all views per call, CUDA graph" if use_graph
                                 else "batched: all views per call, eager", decode="BF16 tcgen05 (FP32 accumulate)" if args.decode == "bf16" else "FP32 SIMT",
-                                tile="16x16", l2="flushed between timed steps (256 MB write)",
+                                tile=tile_desc, blend_batch=tp["blend_batch"],
+                                autotune=[f"{e['tile_w']}x{e['tile_h']}/{e['blend_batch']}: {e['ms']:.3f} ms" for e in tune]
+                                if tune else "off",
+                                l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"replicas x{world}"),
                     plain=dict(value=plain_vps, unit="views/s", form="one view per call sequence, eager, FP32 decoder"),
                     e2e=dict(value=e2e_vps, unit="views/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
@@ -420,6 +440,7 @@ def main():
     ap.add_argument("--workload", default="batch8_1600")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (16x16 tiles, batch 256)")
     ap.add_argument("--decode", default="bf16", choices=("bf16", "fp32"), help="decoder precision of the batched form")
     ap.add_argument("--cap-pairs", type=int, default=None, help="pair capacity (default 2^29)")
     ap.add_argument("--cap-rows", type=int, default=None, help="visible (view, anchor) row capacity")

@@ -91,6 +91,8 @@ typedef struct pgs_render_params {
   int32_t tile_h;
   int32_t decode_precision;   /* pgs_decode_precision (anchor mode) */
   int32_t in_dim;      /* decoder input: 35 = feature + unit view direction (36 adds distance) */
+  int32_t blend_batch; /* Gaussians staged in shared memory per round of the forward blend:
+                          128, 256 (default) or 512; no effect on the results */
 } pgs_render_params;
 
 typedef struct pgs_scene_desc {
@@ -245,6 +247,31 @@ enum pgs_stage {
 };
 pgs_status pgs_set_profiling(pgs_scene* s, int enable);
 pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);
+
+/* Launch-shape autotuner (no counterpart in the paper: it only picks how the
+ * work of Eq. 5-7 is laid out on the GPU, never what is computed).  For every
+ * tile shape (16x16, 8x32, 32x8) and forward shared-memory batch (128, 256,
+ * 512 Gaussians) it runs pgs_render_batch + pgs_backward on the caller's
+ * batch and buffers once untimed and `reps` times timed with CUDA events on
+ * `stream`, keeps the combination with the smallest median time in the
+ * scene's parameters, and caches it per workload signature (device, mode,
+ * number of primitives, view resolutions): a later call with the same
+ * signature applies the cached choice without timing.  Images and buffers
+ * are laid out as for pgs_render_batch / pgs_backward; afterwards the images
+ * hold the last render and the parameter gradients hold the sum of all the
+ * tuning passes (zero them before the next step).  If `entries` is not null
+ * it receives up to max_entries timed combinations (ms < 0 when the choice
+ * came from the cache) and *n_entries their number.  Synchronises the
+ * stream; PGS_ERR_INVALID_ARG while the stream is being captured. */
+typedef struct pgs_tune_entry {
+  int32_t tile_w, tile_h, blend_batch;
+  float ms;                     /* median of the timed render + backward passes */
+} pgs_tune_entry;
+pgs_status pgs_autotune(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                        const pgs_image_grad_ptrs* grad, const pgs_param_grad_ptrs* pg, int reps,
+                        pgs_tune_entry* entries, int max_entries, int* n_entries, cudaStream_t stream);
+/* The scene's current render parameters (as created, or as the autotuner set them). */
+pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out);
 
 /* Workspace buffers of the last render, for tests and tools (device
  * pointers owned by the scene, valid until the next render or destroy):

@@ -52,7 +52,8 @@ class RenderParams(C.Structure):
     _fields_ = [("near_plane", C.c_float), ("dilation", C.c_float), ("alpha_min", C.c_float),
                 ("alpha_max", C.c_float), ("t_min", C.c_float), ("jclamp", C.c_float), ("tile_pad", C.c_float),
                 ("lod_d0", C.c_float), ("n_levels", C.c_int32), ("bg", C.c_float), ("tile_w", C.c_int32),
-                ("tile_h", C.c_int32), ("decode_precision", C.c_int32), ("in_dim", C.c_int32)]
+                ("tile_h", C.c_int32), ("decode_precision", C.c_int32), ("in_dim", C.c_int32),
+                ("blend_batch", C.c_int32)]
 
 
 class SceneDesc(C.Structure):
@@ -102,11 +103,16 @@ class Stats(C.Structure):
                 ("tiles", C.c_int64), ("pixels", C.c_int64), ("flags", C.c_uint32)]
 
 
+class TuneEntry(C.Structure):
+    _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("blend_batch", C.c_int32), ("ms", C.c_float)]
+
+
 ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pgs_scene_create", "pgs_scene_destroy",
                 "pgs_scene_bind_explicit", "pgs_scene_bind_anchors", "pgs_decode_anchors", "pgs_render_batch",
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
-                "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc")
+                "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
+                "pgs_scene_get_params")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad")
 
 
@@ -142,6 +148,9 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_scan_scratch_bytes.restype = C.c_size_t
     L.pgs_exclusive_scan_u32.argtypes = [vp, vp, vp, vp, vp, vp, C.c_size_t, vp]
     L.pgs_sort_pairs_noalloc.argtypes = [vp, vp, i64, i32, i32, vp, vp]
+    L.pgs_autotune.argtypes = [vp, P(Camera), i32, P(ImagePtrs), P(ImageGradPtrs), P(ParamGradPtrs), i32,
+                               P(TuneEntry), i32, P(i32), vp]
+    L.pgs_scene_get_params.argtypes = [vp, P(RenderParams)]
 
 
 def check(status: int) -> None:
@@ -328,6 +337,23 @@ class Scene:
         cc = packed if packed is not None else pack_cameras(cams)
         check(lib().pgs_backward(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(grads.ptrs()),
                                  C.byref(pg), _stream(stream)))
+
+    def autotune(self, cams, images: Images, grads: ImageGrads, param_grads: Dict[str, torch.Tensor], reps: int = 3,
+                 stream=None, packed=None) -> List[dict]:
+        """Pick tile shape and forward shared-memory batch by timing (pgs_autotune); returns the
+        timed combinations (one entry with ms = -1 when the choice came from the cache)."""
+        pg = ParamGradPtrs(*[_ptr(param_grads.get(n)) for n in PARAM_GRAD_FIELDS])
+        cc = packed if packed is not None else pack_cameras(cams)
+        out = (TuneEntry * 16)()
+        n = C.c_int(0)
+        check(lib().pgs_autotune(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(grads.ptrs()),
+                                 C.byref(pg), reps, out, 16, C.byref(n), _stream(stream)))
+        return [dict(tile_w=e.tile_w, tile_h=e.tile_h, blend_batch=e.blend_batch, ms=e.ms) for e in out[:n.value]]
+
+    def params(self) -> dict:
+        p = RenderParams()
+        check(lib().pgs_scene_get_params(self.handle, C.byref(p)))
+        return {k: getattr(p, k) for k, _ in RenderParams._fields_}
 
     def decode(self, cams, capacity_rows: int, stream=None):
         dev = "cuda"

@@ -19,13 +19,14 @@ namespace pgs {
 // scaled conic: power (log2 units) = A' dx^2 + C' dy^2 + B' dx dy
 constexpr float kHalfLog2e = -0.5f * kLog2e;
 constexpr float kNegLog2e = -kLog2e;
-constexpr int kBatch = 256;   // records staged per round (two per thread)
-
+// Records staged in shared memory per round of the forward (NB: 128, 256 or
+// 512, one to four per thread of the 128-thread CTA); picked by the autotuner.
+template <int NB>
 struct BlendSmem {
-  float2 m[kBatch];    // mean relative to the block origin
-  float4 q[kBatch];    // (A', B', C', opacity)
-  float4 c[kBatch];    // (r, g, b, d)
-  float4 n[kBatch];    // (nx, ny, nz, p_lo): p_lo = log2(alpha_min / opacity)
+  float2 m[NB];    // mean relative to the block origin
+  float4 q[NB];    // (A', B', C', opacity)
+  float4 c[NB];    // (r, g, b, d)
+  float4 n[NB];    // (nx, ny, nz, p_lo): p_lo = log2(alpha_min / opacity)
 };
 
 // The alpha >= alpha_min rule is taken on the exponent, o 2^p >= alpha_min <=>
@@ -53,7 +54,8 @@ __device__ __forceinline__ int block_origin(int p0) { return p0 & ~(kOriginBlock
 __device__ __forceinline__ float2 tile_mean(const float4 m, float ox, float oy) {
   return make_float2(__fadd_rn(__fsub_rn(m.x, ox), m.z), __fadd_rn(__fsub_rn(m.y, oy), m.w));
 }
-__device__ __forceinline__ void stage_record(BlendSmem& s, int slot, const float4* __restrict__ rec, uint32_t g,
+template <int NB>
+__device__ __forceinline__ void stage_record(BlendSmem<NB>& s, int slot, const float4* __restrict__ rec, uint32_t g,
                                              float a_min, float ox, float oy) {
   const RecF r = load_record(rec, g, a_min);
   s.m[slot] = tile_mean(r.m, ox, oy);
@@ -134,12 +136,12 @@ __device__ __forceinline__ void warp_block_pixel(int tx, int ty, int TH, int& px
   px = tx * TW + (w % WX) * 8 + (l & 7);
   py0 = ty * TH + (w / WX) * 8 + 2 * (l >> 3);
 }
-template <int TW, int TH>
-__device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, BlendSmem& s,
+template <int TW, int TH, int NB>
+__device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, BlendSmem<NB>& s,
                                                const float4* __restrict__ rec, const uint32_t* __restrict__ pair_g,
                                                const uint2* __restrict__ ranges, const pgs_image_ptrs& out) {
   constexpr int NT = TW * TH / 2;
-  static_assert(2 * NT == kBatch, "two records per thread per round");
+  static_assert(NB % NT == 0, "whole records per thread per round");
   const int vi = view_of_tile(b, tile);
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
@@ -153,13 +155,15 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max, t_min = b.p.t_min;
   PixF P0{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 < v.H)};
   PixF P1{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 + 1 < v.H)};
-  for (uint32_t start = rg.x; start < rg.y; start += kBatch) {
+  for (uint32_t start = rg.x; start < rg.y; start += NB) {
     if (__syncthreads_count(!(P0.done && P1.done)) == 0) break;
-    const uint32_t j0 = start + threadIdx.x, j1 = j0 + NT;
-    if (j0 < rg.y) stage_record(s, threadIdx.x, rec, pair_g[j0], a_min, ox, oy);
-    if (j1 < rg.y) stage_record(s, threadIdx.x + NT, rec, pair_g[j1], a_min, ox, oy);
+#pragma unroll
+    for (int h = 0; h < NB / NT; ++h) {
+      const uint32_t jj = start + threadIdx.x + h * NT;
+      if (jj < rg.y) stage_record(s, threadIdx.x + h * NT, rec, pair_g[jj], a_min, ox, oy);
+    }
     __syncthreads();
-    const int cnt = min((uint32_t)kBatch, rg.y - start);
+    const int cnt = min((uint32_t)NB, rg.y - start);
     for (int k = 0; k < cnt; ++k) {
       if (__all_sync(0xffffffffu, P0.done && P1.done)) break;
       const float4 q = s.q[k];
@@ -457,14 +461,14 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
 
 // Persistent kernels: one resident wave of CTAs takes tiles from a global queue
 // in the given order (longest lists first), so long tiles do not form a tail.
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant__ BatchDev b,
                                                            const float4* __restrict__ rec,
                                                            const uint32_t* __restrict__ pair_g,
                                                            const uint2* __restrict__ ranges, pgs_image_ptrs out,
                                                            const uint32_t* __restrict__ order,
                                                            uint32_t* __restrict__ counter) {
-  __shared__ BlendSmem s;
+  __shared__ BlendSmem<NB> s;
   __shared__ uint32_t s_next;
   for (;;) {
     __syncthreads();
@@ -472,7 +476,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant
     __syncthreads();
     const uint32_t it = s_next;
     if (it >= (uint32_t)b.total_tiles) break;
-    blend_fwd_tile<TW, TH>(b, (int)order[it], s, rec, pair_g, ranges, out);
+    blend_fwd_tile<TW, TH, NB>(b, (int)order[it], s, rec, pair_g, ranges, out);
   }
 }
 
@@ -497,7 +501,7 @@ __global__ void __launch_bounds__(32 * kBwdWarps) k_blend_bwd(const __grid_const
 }
 
 // one resident wave: SMs x CTAs per SM, queried once per kernel instantiation
-template <int TW, int TH, bool BWD, typename K>
+template <int TW, int TH, int NB, bool BWD, typename K>
 static int resident_grid(K kernel, int threads, int total) {
   static int per_sm = -1, sms = 0;
   if (per_sm < 0) {
@@ -510,18 +514,28 @@ static int resident_grid(K kernel, int threads, int total) {
   return std::max(1, std::min(total, per_sm * sms));
 }
 
-template <int TW, int TH>
+template <int TW, int TH, int NB>
 static void launch_fwd_t(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
                          const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
-  const int grid = resident_grid<TW, TH, false>(k_blend_fwd<TW, TH>, TW * TH / 2, b.total_tiles);
-  k_blend_fwd<TW, TH><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
+  const int grid = resident_grid<TW, TH, NB, false>(k_blend_fwd<TW, TH, NB>, TW * TH / 2, b.total_tiles);
+  k_blend_fwd<TW, TH, NB><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
+}
+template <int TW, int TH>
+static bool launch_fwd_nb(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
+                          const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
+  switch (b.p.blend_batch) {
+    case 128: launch_fwd_t<TW, TH, 128>(b, rec, pg, rg, o, order, ctr, st); return true;
+    case 256: launch_fwd_t<TW, TH, 256>(b, rec, pg, rg, o, order, ctr, st); return true;
+    case 512: launch_fwd_t<TW, TH, 512>(b, rec, pg, rg, o, order, ctr, st); return true;
+    default: return false;
+  }
 }
 template <int TW, int TH>
 static void launch_bwd_t(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
                          const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi, float* grad, const uint32_t* order,
                          uint32_t* ctr, cudaStream_t st) {
   static_assert(TW * TH == kTilePix, "256-pixel tiles");
-  const int grid = resident_grid<TW, TH, true>(k_blend_bwd<TW>, 32 * kBwdWarps,
+  const int grid = resident_grid<TW, TH, 0, true>(k_blend_bwd<TW>, 32 * kBwdWarps,
                                               (b.total_tiles + kBwdWarps - 1) / kBwdWarps);
   k_blend_bwd<TW><<<grid, 32 * kBwdWarps, 0, st>>>(b, rec, pg, rg, img, gi, grad, order, ctr);
 }
@@ -529,11 +543,10 @@ static void launch_bwd_t(const BatchDev& b, const float4* rec, const uint32_t* p
 bool launch_blend_fwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
                       const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
   const int tw = b.p.tile_w, th = b.p.tile_h;
-  if (tw == 16 && th == 16) launch_fwd_t<16, 16>(b, rec, pg, rg, o, order, ctr, st);
-  else if (tw == 8 && th == 32) launch_fwd_t<8, 32>(b, rec, pg, rg, o, order, ctr, st);
-  else if (tw == 32 && th == 8) launch_fwd_t<32, 8>(b, rec, pg, rg, o, order, ctr, st);
-  else return false;
-  return true;
+  if (tw == 16 && th == 16) return launch_fwd_nb<16, 16>(b, rec, pg, rg, o, order, ctr, st);
+  if (tw == 8 && th == 32) return launch_fwd_nb<8, 32>(b, rec, pg, rg, o, order, ctr, st);
+  if (tw == 32 && th == 8) return launch_fwd_nb<32, 8>(b, rec, pg, rg, o, order, ctr, st);
+  return false;
 }
 
 bool launch_blend_bwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,

@@ -6,7 +6,10 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
@@ -16,6 +19,10 @@ using namespace pgs;
 namespace {
 
 thread_local std::string g_last_error;
+
+// autotuner choices per workload signature, process-wide
+std::mutex g_tune_mu;
+std::map<std::string, pgs_tune_entry> g_tune_cache;
 
 pgs_status fail(pgs_status s, const char* fmt, ...) {
   char buf[512];
@@ -149,6 +156,7 @@ void pgs_default_params(pgs_render_params* p) {
   p->tile_h = 16;
   p->decode_precision = PGS_DECODE_FP32;
   p->in_dim = 35;
+  p->blend_batch = 256;
 }
 
 void pgs_scene_destroy(pgs_scene* s) {
@@ -184,6 +192,8 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
                        (p.tile_w == 32 && p.tile_h == 8);
   if (!tile_ok) return fail(PGS_ERR_INVALID_ARG, "tile shape %dx%d (16x16, 8x32, 32x8)", p.tile_w, p.tile_h);
   if (p.in_dim != 35 && p.in_dim != 36) return fail(PGS_ERR_INVALID_ARG, "in_dim %d (35 or 36)", p.in_dim);
+  if (p.blend_batch != 128 && p.blend_batch != 256 && p.blend_batch != 512)
+    return fail(PGS_ERR_INVALID_ARG, "blend_batch %d (128, 256 or 512)", p.blend_batch);
   if (p.n_levels < 1 || p.n_levels > 16) return fail(PGS_ERR_INVALID_ARG, "n_levels %d", p.n_levels);
   if (!(p.alpha_min > 0.f && p.alpha_min < p.alpha_max && p.alpha_max < 1.f && p.t_min > 0.f && p.near_plane > 0.f))
     return fail(PGS_ERR_INVALID_ARG, "render thresholds out of range");
@@ -292,6 +302,7 @@ pgs_status build_batch(pgs_scene* s, const pgs_camera* cams, int n_views, BatchD
   b.p.near_plane = p.near_plane; b.p.dilation = p.dilation; b.p.alpha_min = p.alpha_min; b.p.alpha_max = p.alpha_max;
   b.p.t_min = p.t_min; b.p.jclamp = p.jclamp; b.p.tile_pad = p.tile_pad; b.p.lod_d0 = p.lod_d0; b.p.bg = p.bg;
   b.p.n_levels = p.n_levels; b.p.tile_w = p.tile_w; b.p.tile_h = p.tile_h; b.p.in_dim = p.in_dim;
+  b.p.blend_batch = p.blend_batch;
   b.n_views = n_views;
   long long pix = 0;
   long long tiles = 0;
@@ -524,6 +535,94 @@ pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n) {
     PGS_CUDA(cudaEventSynchronize(s->ev[k][1]));
     PGS_CUDA(cudaEventElapsedTime(&ms[k], s->ev[k][0], s->ev[k][1]));
   }
+  return PGS_OK;
+}
+
+pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out) {
+  if (!s || !out) return fail(PGS_ERR_INVALID_ARG, "null argument");
+  *out = s->d.params;
+  return PGS_OK;
+}
+
+pgs_status pgs_autotune(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                        const pgs_image_grad_ptrs* grad, const pgs_param_grad_ptrs* pg, int reps,
+                        pgs_tune_entry* entries, int max_entries, int* n_entries, cudaStream_t st) {
+  if (n_entries) *n_entries = 0;
+  if (!s || !cams || !img || !grad || !pg) return fail(PGS_ERR_INVALID_ARG, "null argument");
+  if (n_views <= 0 || n_views > s->d.max_views) return fail(PGS_ERR_INVALID_ARG, "n_views %d", n_views);
+  if (reps < 1 || reps > 100) return fail(PGS_ERR_INVALID_ARG, "reps %d (1..100)", reps);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  PGS_CUDA(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return fail(PGS_ERR_INVALID_ARG, "pgs_autotune during stream capture");
+  // workload signature
+  std::string key = std::to_string(s->device) + "/" + std::to_string(s->d.mode) + "/" +
+                    std::to_string(s->d.n_primitives);
+  for (int v = 0; v < n_views; ++v) key += "/" + std::to_string(cams[v].width) + "x" + std::to_string(cams[v].height);
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune_cache.find(key);
+    if (it != g_tune_cache.end()) {
+      s->d.params.tile_w = it->second.tile_w;
+      s->d.params.tile_h = it->second.tile_h;
+      s->d.params.blend_batch = it->second.blend_batch;
+      if (entries && max_entries > 0) {
+        entries[0] = it->second;
+        entries[0].ms = -1.f;
+        if (n_entries) *n_entries = 1;
+      }
+      return PGS_OK;
+    }
+  }
+  static const int shapes[3][2] = {{16, 16}, {8, 32}, {32, 8}};
+  static const int batches[3] = {128, 256, 512};
+  const pgs_render_params saved = s->d.params;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  PGS_CUDA(cudaEventCreate(&e0));
+  PGS_CUDA(cudaEventCreate(&e1));
+  pgs_tune_entry best{saved.tile_w, saved.tile_h, saved.blend_batch, 3.4e38f};
+  int n = 0;
+  pgs_status r = PGS_OK;
+  for (const auto& sh : shapes) {
+    for (int nb : batches) {
+      s->d.params.tile_w = sh[0];
+      s->d.params.tile_h = sh[1];
+      s->d.params.blend_batch = nb;
+      std::vector<float> t;
+      for (int k = 0; k <= reps && r == PGS_OK; ++k) {
+        if (k > 0) cudaEventRecord(e0, st);
+        r = pgs_render_batch(s, cams, n_views, img, st);
+        if (r == PGS_OK) r = pgs_backward(s, cams, n_views, img, grad, pg, st);
+        if (k > 0 && r == PGS_OK) {
+          cudaEventRecord(e1, st);
+          float ms = 0.f;
+          if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            r = fail(PGS_ERR_CUDA, "autotune timing: %s", cudaGetErrorString(cudaGetLastError()));
+            break;
+          }
+          t.push_back(ms);
+        }
+      }
+      if (r != PGS_OK) break;
+      std::sort(t.begin(), t.end());
+      const pgs_tune_entry e{sh[0], sh[1], nb, t[t.size() / 2]};
+      if (entries && n < max_entries) entries[n] = e;
+      ++n;
+      if (e.ms < best.ms) best = e;
+    }
+    if (r != PGS_OK) break;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (r != PGS_OK) {
+    s->d.params = saved;
+    return r;
+  }
+  if (n_entries) *n_entries = std::min(n, max_entries);
+  s->d.params.tile_w = best.tile_w;
+  s->d.params.tile_h = best.tile_h;
+  s->d.params.blend_batch = best.blend_batch;
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune_cache[key] = best;
   return PGS_OK;
 }
 

@@ -35,7 +35,7 @@ struct ViewDev {
 
 struct ParamsDev {
   float near_plane, dilation, alpha_min, alpha_max, t_min, jclamp, tile_pad, lod_d0, bg;
-  int n_levels, tile_w, tile_h, in_dim;
+  int n_levels, tile_w, tile_h, in_dim, blend_batch;
 };
 
 struct BatchDev {

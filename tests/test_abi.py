@@ -39,7 +39,8 @@ def test_library_exports_every_declared_symbol():
 
 def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(B.Camera) == 18 * 4
-    assert ctypes.sizeof(B.RenderParams) == 14 * 4
+    assert ctypes.sizeof(B.RenderParams) == 15 * 4
+    assert ctypes.sizeof(B.TuneEntry) == 4 * 4
     assert ctypes.sizeof(B.ImagePtrs) == 8 * 8
     assert ctypes.sizeof(B.ParamGradPtrs) == 13 * 8
     assert ctypes.sizeof(B.Stats) == 7 * 8
@@ -49,7 +50,7 @@ def test_default_params_and_argument_errors_without_gpu():
     _lib()
     p = B.default_params()
     assert abs(p.alpha_min - 1 / 255) < 1e-9 and p.alpha_max == pytest.approx(0.99) and p.t_min == pytest.approx(1e-4)
-    assert p.tile_w == 16 and p.tile_h == 16 and p.in_dim == 35
+    assert p.tile_w == 16 and p.tile_h == 16 and p.in_dim == 35 and p.blend_batch == 256
     L = B.lib()
     h = ctypes.c_void_p()
     bad = B.SceneDesc(mode=7, n_primitives=10, max_views=1, max_pixels=100, capacity_rows=0, capacity_pairs=100,
@@ -61,6 +62,10 @@ def test_default_params_and_argument_errors_without_gpu():
     assert L.pgs_scene_create(ctypes.byref(bad), ctypes.byref(h)) == B.PGS_ERR_INVALID_ARG
     assert b"tile shape" in L.pgs_last_error()
     bad.params.tile_w = 16
+    bad.params.blend_batch = 100
+    assert L.pgs_scene_create(ctypes.byref(bad), ctypes.byref(h)) == B.PGS_ERR_INVALID_ARG
+    assert b"blend_batch" in L.pgs_last_error()
+    bad.params.blend_batch = 256
     bad.capacity_pairs = 1 << 31
     assert L.pgs_scene_create(ctypes.byref(bad), ctypes.byref(h)) == B.PGS_ERR_INVALID_ARG
     assert L.pgs_status_string(B.PGS_ERR_TIMEOUT) == b"bounded wait timed out"
