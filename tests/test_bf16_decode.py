@@ -42,7 +42,7 @@ def test_tensor_core_decoder_matches_fp32_decoder(n_anchors):
 
 def test_bf16_images_against_fp64_oracle_tiny():
     sc = synth.tiny_anchor_scene(n_anchors=6, seed=3, n_views=2, width=48, height=40)
-    orc = O.render(sc, O.RenderParams())
+    orc = O.render(sc, O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"])))
     scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=B.DECODE_BF16))
     img = scene.render(sc["cameras"])
     scene.read_status()
@@ -58,7 +58,8 @@ def test_bf16_images_against_fp64_oracle_1080p_crop(seed):
     cam = sc["cameras"][0]
     rng = np.random.default_rng(seed)
     crop = (int(rng.integers(0, cam.width - 64)), int(rng.integers(cam.height // 3, cam.height - 64)), 64, 64)
-    orc = O.render(sc, O.RenderParams(), crops=[crop])["views"][0]
+    rp = O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
+    orc = O.render(sc, rp, crops=[crop])["views"][0]
     scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=B.DECODE_BF16), cap_rows=len(sc["x"]))
     img = scene.render([cam])
     scene.read_status()
