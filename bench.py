@@ -139,7 +139,10 @@ def build_scene(sc, B, device, cap_pairs=None, cap_rows=None, precision=None):
 
 
 # ------------------------------------------------------------------ CPU oracle baseline
-def cpu_oracle_sample(sc, targets, view: int, crop_size: int = 64):
+CPU_CROP = 128   # oracle crop side: 8 views x (setup + 128^2 crop fwd+bwd) is about 10-15 s of CPU work
+
+
+def cpu_oracle_sample(sc, targets, view: int, crop_size: int = CPU_CROP):
     """FP64 oracle on one view: decode + project every LoD-active anchor, then a
     crop_size^2 crop forward + backward (seeded image gradient).  Returns
     (seconds of the whole-view setup, seconds of the crop, crop pixels)."""
@@ -162,7 +165,7 @@ def cpu_oracle_sample(sc, targets, view: int, crop_size: int = 64):
     return t1 - t0, t2 - t1, crop_size * crop_size
 
 
-def cpu_views_per_s(sc, targets, views, crop_size=64):
+def cpu_views_per_s(sc, targets, views, crop_size=CPU_CROP):
     total_t, parts = 0.0, []
     for v in views:
         ts, tc, npx = cpu_oracle_sample(sc, targets, v, crop_size)
@@ -192,7 +195,7 @@ def run_reference(args):
     cores = torch.get_num_threads()
     sample = (f"per step one of the {V} views ({resolution_desc(sc['cameras'])}): FP64 decode+projection of every "
               "LoD-active anchor, then a "
-              "64x64 crop fwd+bwd; per-pixel cost extrapolated to the full frame")
+              f"{CPU_CROP}x{CPU_CROP} crop fwd+bwd; per-pixel cost extrapolated to the full frame")
     line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * sum(timed) / len(timed), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
@@ -401,8 +404,8 @@ def run_pgs(args):
         torch.set_num_threads(max(1, len(os.sched_getaffinity(0))))
         vps, parts = cpu_views_per_s(sc, tviews, list(range(V)))
         cpu = dict(value=vps, unit="views/s", cores=torch.get_num_threads(), kind="oracle",
-                   sample=f"all {V} views: FP64 decode+projection of every LoD-active anchor, then one 64x64 crop "
-                          "fwd+bwd per view; per-pixel cost extrapolated to 1600x1064",
+                   sample=f"all {V} views: FP64 decode+projection of every LoD-active anchor, then one {CPU_CROP}x{CPU_CROP} crop "
+                          "fwd+bwd per view; per-pixel cost extrapolated to the full frame",
                    seconds=dict(setup=sum(p[0] for p in parts), crops=sum(p[1] for p in parts)))
 
     clocks = clk.summary()
