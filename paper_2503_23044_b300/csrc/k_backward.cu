@@ -297,10 +297,10 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
       }
     }
     if (bad) set_flag(err, kFlagNonfinite);
-    // row scratch for the weight gradients (column-major: feature i of row r at i * cap + r)
-    for (int t = 0; t < kOut; ++t) sc_dZ[t * cap + r] = dZ[t];
-    for (int h = 0; h < kHidden; ++h) { sc_H[h * cap + r] = H[h]; sc_dH[h * cap + r] = dH[h]; }
-    for (int j = 0; j < in_dim; ++j) sc_X[j * cap + r] = X[j];
+    // row scratch for the weight gradients, in 32-row blocks (sc_at)
+    for (int t = 0; t < kOut; ++t) sc_dZ[sc_at(r, t, kOut)] = dZ[t];
+    for (int h = 0; h < kHidden; ++h) { sc_H[sc_at(r, h, kHidden)] = H[h]; sc_dH[sc_at(r, h, kHidden)] = dH[h]; }
+    for (int j = 0; j < in_dim; ++j) sc_X[sc_at(r, j, kMaxIn)] = X[j];
   }
 }
 
@@ -312,75 +312,178 @@ constexpr int kWgRows = 32;
 
 __host__ __device__ inline int wgrad_outputs(int in_dim) { return kOut * kHidden + kOut + kHidden * in_dim + kHidden; }
 
+// Each block stages kWgRows rows at a time row-major in shared memory and
+// accumulates register tiles.  Warps 0..5 hold 5 x 4 tiles of dW2 (110 x 32; 176
+// of their 192 threads), warps 6..7 hold 4 x 5 tiles of dW1 (32 x in_dim); a
+// thread whose tile starts at column 0 also sums its rows of dZ (db2) or dH
+// (db1).  Every warp runs one code path, and the next round's scratch is loaded
+// into registers while the current round is summed.
+constexpr int kWgZ = kOut + 1, kWgH = kHidden + 1, kWgX = kMaxIn + 1;   // padded row strides
+constexpr int kWgTilesW2 = (kOut / 5) * (kHidden / 4);                   // 176
+constexpr int kWgTilesW1 = (kHidden / 4) * ((kMaxIn + 4) / 5);           // 64
+constexpr int kWgRole1 = 192;                                            // first dW1 thread (warp 6)
+static_assert(kOut % 5 == 0 && kHidden % 4 == 0, "tile shapes");
+static_assert(kWgTilesW2 <= kWgRole1 && kWgRole1 + kWgTilesW1 == 256, "thread roles");
+
+struct WgStage {
+  static constexpr int kNZ = (kOut * kWgRows + 255) / 256, kNH = kHidden * kWgRows / 256;
+  static constexpr int kNX = (kMaxIn * kWgRows + 255) / 256;
+  float z[kNZ], h[kNH], dh[kNH], x[kNX];
+};
+
+// load one 32-row scratch block (rows rb .. rb + nr - 1) into registers: thread t
+// takes row t % 32 of features t / 32 + 8 k
+__device__ __forceinline__ void wg_load(WgStage& v, const float* __restrict__ sc_dZ, const float* __restrict__ sc_H,
+                                        const float* __restrict__ sc_dH, const float* __restrict__ sc_X, long long rb,
+                                        int nr, int in_dim) {
+  const int t = threadIdx.x, rr = t % kWgRows, i0 = t / kWgRows;
+  const bool rok = rr < nr;
+#pragma unroll
+  for (int k = 0; k < WgStage::kNZ; ++k) {
+    const int i = i0 + 8 * k;
+    v.z[k] = (rok && i < kOut) ? sc_dZ[sc_at(rb + rr, i, kOut)] : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < WgStage::kNH; ++k) {
+    const int i = i0 + 8 * k;
+    v.h[k] = rok ? sc_H[sc_at(rb + rr, i, kHidden)] : 0.f;
+    v.dh[k] = rok ? sc_dH[sc_at(rb + rr, i, kHidden)] : 0.f;
+  }
+#pragma unroll
+  for (int k = 0; k < WgStage::kNX; ++k) {
+    const int i = i0 + 8 * k;
+    v.x[k] = (rok && i < in_dim) ? sc_X[sc_at(rb + rr, i, kMaxIn)] : 0.f;
+  }
+}
+
+// launched with exactly 256 threads (the staging assumes it)
 __global__ void __launch_bounds__(256) k_mlp_wgrad_partial(const float* __restrict__ sc_dZ, const float* __restrict__ sc_H,
                                                            const float* __restrict__ sc_dH, const float* __restrict__ sc_X,
                                                            const long long* __restrict__ n_rows_p, long long cap,
                                                            int in_dim, float* __restrict__ partials) {
-  __shared__ float sZ[kOut][kWgRows + 1];
-  __shared__ float sH[kHidden][kWgRows + 1];
-  __shared__ float sdH[kHidden][kWgRows + 1];
-  __shared__ float sX[kMaxIn][kWgRows + 1];
+  __shared__ float sZ[kWgRows][kWgZ];
+  __shared__ float sH[kWgRows][kWgH];
+  __shared__ float sdH[kWgRows][kWgH];
+  __shared__ float sX[kWgRows][kWgX];
   const long long n = min(*n_rows_p, cap);
-  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  // whole 32-row scratch blocks per CTA, so each round reads one contiguous block per array
+  const long long per = ((n + gridDim.x - 1) / gridDim.x + kScBlock - 1) / kScBlock * kScBlock;
   const long long r0 = min(n, (long long)blockIdx.x * per), r1 = min(n, r0 + per);
   const int n_out = wgrad_outputs(in_dim);
-  constexpr int kMaxPer = 20;
-  float acc[kMaxPer];
-  for (int i = 0; i < kMaxPer; ++i) acc[i] = 0.f;
+  const int t = threadIdx.x;
+  const bool w2 = t < kWgRole1;
+  const bool live = w2 ? t < kWgTilesW2 : true;
+  int fa, gb;
+  if (w2) { fa = (min(t, kWgTilesW2 - 1) / (kHidden / 4)) * 5; gb = (min(t, kWgTilesW2 - 1) % (kHidden / 4)) * 4; }
+  else { const int u = t - kWgRole1; fa = (u / ((kMaxIn + 4) / 5)) * 4; gb = (u % ((kMaxIn + 4) / 5)) * 5; }
+  const bool bias = gb == 0;          // also sums the bias entries of its rows
+  float acc[20], bs[5];
+#pragma unroll
+  for (int i = 0; i < 20; ++i) acc[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < 5; ++i) bs[i] = 0.f;
+  const int rr_s = t % kWgRows, i0_s = t / kWgRows;
+  WgStage v;
+  if (r0 < r1) wg_load(v, sc_dZ, sc_H, sc_dH, sc_X, r0, (int)min((long long)kWgRows, r1 - r0), in_dim);
   for (long long rb = r0; rb < r1; rb += kWgRows) {
-    const int nr = (int)min((long long)kWgRows, r1 - rb);
+    __syncthreads();                  // the previous round's tiles are consumed
+#pragma unroll
+    for (int k = 0; k < WgStage::kNZ; ++k)
+      if (i0_s + 8 * k < kOut) sZ[rr_s][i0_s + 8 * k] = v.z[k];
+#pragma unroll
+    for (int k = 0; k < WgStage::kNH; ++k) { sH[rr_s][i0_s + 8 * k] = v.h[k]; sdH[rr_s][i0_s + 8 * k] = v.dh[k]; }
+#pragma unroll
+    for (int k = 0; k < WgStage::kNX; ++k)
+      if (i0_s + 8 * k < kMaxIn) sX[rr_s][i0_s + 8 * k] = v.x[k];
     __syncthreads();
-    for (int t = threadIdx.x; t < kOut * kWgRows; t += blockDim.x) {
-      const int i = t / kWgRows, rr = t % kWgRows;
-      sZ[i][rr] = rr < nr ? sc_dZ[i * cap + rb + rr] : 0.f;
-    }
-    for (int t = threadIdx.x; t < kHidden * kWgRows; t += blockDim.x) {
-      const int i = t / kWgRows, rr = t % kWgRows;
-      sH[i][rr] = rr < nr ? sc_H[i * cap + rb + rr] : 0.f;
-      sdH[i][rr] = rr < nr ? sc_dH[i * cap + rb + rr] : 0.f;
-    }
-    for (int t = threadIdx.x; t < in_dim * kWgRows; t += blockDim.x) {
-      const int i = t / kWgRows, rr = t % kWgRows;
-      sX[i][rr] = rr < nr ? sc_X[i * cap + rb + rr] : 0.f;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int s = 0; s < kMaxPer; ++s) {
-      const int o = threadIdx.x + s * blockDim.x;
-      if (o >= n_out) break;
-      const float* u;
-      const float* w;
-      if (o < kOut * kHidden) { u = sZ[o / kHidden]; w = sH[o % kHidden]; }
-      else if (o < kOut * kHidden + kOut) { u = sZ[o - kOut * kHidden]; w = nullptr; }
-      else if (o < kOut * kHidden + kOut + kHidden * in_dim) {
-        const int oo = o - kOut * kHidden - kOut;
-        u = sdH[oo / in_dim]; w = sX[oo % in_dim];
-      } else { u = sdH[o - kOut * kHidden - kOut - kHidden * in_dim]; w = nullptr; }
-      float a = acc[s];
-      if (w) { for (int rr = 0; rr < kWgRows; ++rr) a = fmaf(u[rr], w[rr], a); }
-      else { for (int rr = 0; rr < kWgRows; ++rr) a += u[rr]; }
-      acc[s] = a;
+    const long long nb2 = rb + kWgRows;
+    if (nb2 < r1) wg_load(v, sc_dZ, sc_H, sc_dH, sc_X, nb2, (int)min((long long)kWgRows, r1 - nb2), in_dim);
+    if (w2) {
+#pragma unroll 4
+      for (int rr = 0; rr < kWgRows; ++rr) {
+        float u[5], w[4];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) u[a] = sZ[rr][fa + a];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) w[c] = sH[rr][gb + c];
+#pragma unroll
+        for (int a = 0; a < 5; ++a) {
+          bs[a] += u[a];
+#pragma unroll
+          for (int c = 0; c < 4; ++c) acc[a * 4 + c] = fmaf(u[a], w[c], acc[a * 4 + c]);
+        }
+      }
+    } else {
+#pragma unroll 4
+      for (int rr = 0; rr < kWgRows; ++rr) {
+        float u[4], w[5];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) u[a] = sdH[rr][fa + a];
+#pragma unroll
+        for (int c = 0; c < 5; ++c) w[c] = sX[rr][min(gb + c, kMaxIn - 1)];
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+          bs[a] += u[a];
+#pragma unroll
+          for (int c = 0; c < 5; ++c) acc[a * 5 + c] = fmaf(u[a], w[c], acc[a * 5 + c]);
+        }
+      }
     }
   }
-  for (int s = 0; s < kMaxPer; ++s) {
-    const int o = threadIdx.x + s * blockDim.x;
-    if (o < n_out) partials[(long long)blockIdx.x * n_out + o] = acc[s];
+  // outputs in the order W2 (row-major), b2, W1 (row-major, hidden x in_dim), b1
+  float* dst = partials + (long long)blockIdx.x * n_out;
+  if (w2 && live) {
+#pragma unroll
+    for (int a = 0; a < 5; ++a) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) dst[(fa + a) * kHidden + gb + c] = acc[a * 4 + c];
+      if (bias) dst[kOut * kHidden + fa + a] = bs[a];
+    }
+  } else if (!w2) {
+    const int base = kOut * kHidden + kOut;
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+#pragma unroll
+      for (int c = 0; c < 5; ++c)
+        if (gb + c < in_dim) dst[base + (fa + a) * in_dim + gb + c] = acc[a * 5 + c];
+      if (bias) dst[base + kHidden * in_dim + fa + a] = bs[a];
+    }
   }
 }
 
+// Sum of the per-block partials in block order: warp w of a block adds blocks
+// w, w + 8, ... for 32 consecutive outputs, then the 8 warp sums are added in
+// warp order (fixed order, so the result is reproducible).
 __global__ void __launch_bounds__(256) k_mlp_wgrad_final(const float* __restrict__ partials, int nb, int in_dim,
                                                          pgs_param_grad_ptrs out) {
+  __shared__ float s_part[8][32];
   const int n_out = wgrad_outputs(in_dim);
-  for (int o = blockIdx.x * blockDim.x + threadIdx.x; o < n_out; o += gridDim.x * blockDim.x) {
-    float s = 0.f;
-    for (int k = 0; k < nb; ++k) s += partials[(long long)k * n_out + o];
-    float* dst;
-    if (o < kOut * kHidden) dst = out.W2 ? out.W2 + o : nullptr;
-    else if (o < kOut * kHidden + kOut) dst = out.b2 ? out.b2 + (o - kOut * kHidden) : nullptr;
-    else if (o < kOut * kHidden + kOut + kHidden * in_dim) dst = out.W1 ? out.W1 + (o - kOut * kHidden - kOut) : nullptr;
-    else dst = out.b1 ? out.b1 + (o - kOut * kHidden - kOut - kHidden * in_dim) : nullptr;
-    if (dst) *dst += s;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int o = blockIdx.x * 32 + lane;
+  float s = 0.f;
+  if (o < n_out) {
+    int k = w;
+    for (; k + 56 < nb; k += 64) {     // eight independent loads per round, added in block order
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = partials[(long long)(k + 8 * u) * n_out + o];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) s += v[u];
+    }
+    for (; k < nb; k += 8) s += partials[(long long)k * n_out + o];
   }
+  s_part[w][lane] = s;
+  __syncthreads();
+  if (w != 0 || o >= n_out) return;
+  float tot = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) tot += s_part[k][lane];
+  float* dst;
+  if (o < kOut * kHidden) dst = out.W2 ? out.W2 + o : nullptr;
+  else if (o < kOut * kHidden + kOut) dst = out.b2 ? out.b2 + (o - kOut * kHidden) : nullptr;
+  else if (o < kOut * kHidden + kOut + kHidden * in_dim) dst = out.W1 ? out.W1 + (o - kOut * kHidden - kOut) : nullptr;
+  else dst = out.b1 ? out.b1 + (o - kOut * kHidden - kOut - kHidden * in_dim) : nullptr;
+  if (dst) *dst += tot;
 }
 
 int mlp_wgrad_outputs(int in_dim) { return wgrad_outputs(in_dim); }
@@ -389,7 +492,7 @@ void launch_mlp_wgrad(const float* dZ, const float* H, const float* dH, const fl
                       long long cap, int in_dim, float* partials, int nb, const pgs_param_grad_ptrs& out,
                       cudaStream_t st) {
   k_mlp_wgrad_partial<<<nb, 256, 0, st>>>(dZ, H, dH, X, n_rows, cap, in_dim, partials);
-  k_mlp_wgrad_final<<<(wgrad_outputs(in_dim) + 255) / 256, 256, 0, st>>>(partials, nb, in_dim, out);
+  k_mlp_wgrad_final<<<(wgrad_outputs(in_dim) + 31) / 32, 256, 0, st>>>(partials, nb, in_dim, out);
 }
 
 }  // namespace pgs

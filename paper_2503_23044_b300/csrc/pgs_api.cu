@@ -244,10 +244,10 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
     ALLOC(s->cull_flags, s->n_cull);
     ALLOC(s->cull_offs, s->n_cull);
     ALLOC(s->rows, s->cap_rows);
-    ALLOC(s->sc_dZ, s->cap_rows * kOut);
-    ALLOC(s->sc_H, s->cap_rows * kHidden);
-    ALLOC(s->sc_dH, s->cap_rows * kHidden);
-    ALLOC(s->sc_X, s->cap_rows * kMaxIn);
+    ALLOC(s->sc_dZ, sc_rows(s->cap_rows) * kOut);
+    ALLOC(s->sc_H, sc_rows(s->cap_rows) * kHidden);
+    ALLOC(s->sc_dH, sc_rows(s->cap_rows) * kHidden);
+    ALLOC(s->sc_X, sc_rows(s->cap_rows) * kMaxIn);
     s->wg_blocks = 2 * s->num_sms;
     ALLOC(s->wg_partials, (long long)s->wg_blocks * mlp_wgrad_outputs(kMaxIn));
   }

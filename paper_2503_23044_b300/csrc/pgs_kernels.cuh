@@ -75,6 +75,15 @@ void launch_loss(const BatchDev& b, const pgs_image_ptrs& img, const pgs_target_
                  float* loss, const pgs_image_grad_ptrs& g, uint32_t* counts, float* partials, uint32_t* err,
                  cudaStream_t st);
 
+// Decoder backward row scratch (dZ, H, dH, X per visible row): rows in blocks of
+// kScBlock, feature-major inside a block, so a warp's 32 consecutive rows write
+// one contiguous run per feature and a block of rows is one contiguous chunk.
+constexpr int kScBlock = 32;
+__host__ __device__ __forceinline__ size_t sc_at(long long r, int f, int width) {
+  return ((size_t)(r / kScBlock) * width + f) * kScBlock + (size_t)(r % kScBlock);
+}
+__host__ __device__ __forceinline__ long long sc_rows(long long cap) { return (cap + kScBlock - 1) / kScBlock * kScBlock; }
+
 // k_backward.cu
 __global__ void k_project_bwd_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N,
                                        const float* grad, pgs_param_grad_ptrs out, uint32_t* err);
