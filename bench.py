@@ -252,6 +252,7 @@ def run_pgs(args):
     scene.read_status(stream)
     n_eval = float(images.n_eval.double().sum())
     n_contrib = float(images.n_contrib.double().sum())
+    images = images.without_stats()     # the timed step renders without the diagnostic counts
 
     # launch-shape autotuner (tile shape x shared-memory batch), outside the timed region
     tune = []

@@ -216,19 +216,23 @@ class Images:
     dist: torch.Tensor
     t_final: torch.Tensor
     last: torch.Tensor
-    n_contrib: torch.Tensor
-    n_eval: torch.Tensor
+    n_contrib: Optional[torch.Tensor]   # diagnostic per-pixel counts; None skips them (faster forward)
+    n_eval: Optional[torch.Tensor]
     offsets: List[int]
     shapes: List[tuple]
 
     @staticmethod
-    def empty(cams, device="cuda") -> "Images":
+    def empty(cams, device="cuda", stats: bool = True) -> "Images":
         off = arena_offsets(cams)
         n = off[-1]
         f = lambda k: torch.zeros(k, device=device, dtype=torch.float32)
         i = lambda k: torch.zeros(k, device=device, dtype=torch.int32)
-        return Images(f(3 * n), f(n), f(3 * n), f(n), f(n), i(n), i(n), i(n), off,
-                      [(int(c.height), int(c.width)) for c in cams])
+        return Images(f(3 * n), f(n), f(3 * n), f(n), f(n), i(n), i(n) if stats else None, i(n) if stats else None,
+                      off, [(int(c.height), int(c.width)) for c in cams])
+
+    def without_stats(self) -> "Images":
+        """The same buffers with the diagnostic counts switched off."""
+        return dataclasses.replace(self, n_contrib=None, n_eval=None)
 
     def ptrs(self) -> ImagePtrs:
         return ImagePtrs(_ptr(self.rgb), _ptr(self.depth), _ptr(self.normal), _ptr(self.dist), _ptr(self.t_final),
@@ -239,7 +243,9 @@ class Images:
         a, b = self.offsets[v], self.offsets[v + 1]
         out = dict(rgb=self.rgb[3 * a:3 * b].view(3, H, W), normal=self.normal[3 * a:3 * b].view(3, H, W))
         for k in ("depth", "dist", "t_final", "last", "n_contrib", "n_eval"):
-            out[k] = getattr(self, k)[a:b].view(H, W)
+            t = getattr(self, k)
+            if t is not None:
+                out[k] = t[a:b].view(H, W)
         return out
 
 

@@ -84,6 +84,8 @@ struct PixF {            // forward state of one pixel
 // Take (or not) one record at a pixel whose power test gave `take`, with every
 // step predicated: alpha, the stop rule T_new < t_min (the pixel ends before
 // this record) and the masked accumulation.
+// STATS: also count the pixel's contributors and evaluations (diagnostic outputs).
+template <bool STATS>
 __device__ __forceinline__ void fwd_take(PixF& P, bool take, float power, float opac, const float4 c,
                                          const float4 nn, uint32_t j, float a_max, float t_min) {
   const float a_raw = __fmul_rn(opac, ex2_approx(power));
@@ -96,8 +98,10 @@ __device__ __forceinline__ void fwd_take(PixF& P, bool take, float power, float 
   P.n0 = fmaf(w, nn.x, P.n0); P.n1 = fmaf(w, nn.y, P.n1); P.n2 = fmaf(w, nn.z, P.n2);
   P.T = cont ? Tn : P.T;
   P.last = cont ? j + 1 : P.last;
-  P.ncontrib += cont ? 1u : 0u;
-  P.stop = stop ? j + 1 : P.stop;
+  if (STATS) {
+    P.ncontrib += cont ? 1u : 0u;
+    P.stop = stop ? j + 1 : P.stop;
+  }
   P.done = P.done || stop;
 }
 
@@ -136,7 +140,7 @@ __device__ __forceinline__ void warp_block_pixel(int tx, int ty, int TH, int& px
   px = tx * TW + (w % WX) * 8 + (l & 7);
   py0 = ty * TH + (w / WX) * 8 + 2 * (l >> 3);
 }
-template <int TW, int TH, int NB>
+template <int TW, int TH, int NB, bool STATS>
 __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, BlendSmem<NB>& s,
                                                const float4* __restrict__ rec, const uint32_t* __restrict__ pair_g,
                                                const uint2* __restrict__ ranges, const pgs_image_ptrs& out) {
@@ -165,7 +169,7 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
     __syncthreads();
     const int cnt = min((uint32_t)NB, rg.y - start);
     for (int k = 0; k < cnt; ++k) {
-      if (__all_sync(0xffffffffu, P0.done && P1.done)) break;
+      if ((k & 3) == 0 && __all_sync(0xffffffffu, P0.done && P1.done)) break;
       const float4 q = s.q[k];
       const float2 m = s.m[k];
       const float p_lo = s.n[k].w;
@@ -178,8 +182,8 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
       if (!__any_sync(0xffffffffu, t0 || t1)) continue;
       const float4 c = s.c[k], nn = s.n[k];
       const uint32_t j = start + k;
-      fwd_take(P0, t0, pw0, q.w, c, nn, j, a_max, t_min);
-      fwd_take(P1, t1, pw1, q.w, c, nn, j, a_max, t_min);
+      fwd_take<STATS>(P0, t0, pw0, q.w, c, nn, j, a_max, t_min);
+      fwd_take<STATS>(P1, t1, pw1, q.w, c, nn, j, a_max, t_min);
     }
   }
   fwd_write(P0, v, b.p, px, py0, rg.x, out);
@@ -461,7 +465,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
 
 // Persistent kernels: one resident wave of CTAs takes tiles from a global queue
 // in the given order (longest lists first), so long tiles do not form a tail.
-template <int TW, int TH, int NB>
+template <int TW, int TH, int NB, bool STATS>
 __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant__ BatchDev b,
                                                            const float4* __restrict__ rec,
                                                            const uint32_t* __restrict__ pair_g,
@@ -476,7 +480,7 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant
     __syncthreads();
     const uint32_t it = s_next;
     if (it >= (uint32_t)b.total_tiles) break;
-    blend_fwd_tile<TW, TH, NB>(b, (int)order[it], s, rec, pair_g, ranges, out);
+    blend_fwd_tile<TW, TH, NB, STATS>(b, (int)order[it], s, rec, pair_g, ranges, out);
   }
 }
 
@@ -517,8 +521,13 @@ static int resident_grid(K kernel, int threads, int total) {
 template <int TW, int TH, int NB>
 static void launch_fwd_t(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
                          const pgs_image_ptrs& o, const uint32_t* order, uint32_t* ctr, cudaStream_t st) {
-  const int grid = resident_grid<TW, TH, NB, false>(k_blend_fwd<TW, TH, NB>, TW * TH / 2, b.total_tiles);
-  k_blend_fwd<TW, TH, NB><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
+  if (o.n_contrib || o.n_eval) {
+    const int grid = resident_grid<TW, TH, 2 * NB + 1, false>(k_blend_fwd<TW, TH, NB, true>, TW * TH / 2, b.total_tiles);
+    k_blend_fwd<TW, TH, NB, true><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
+  } else {
+    const int grid = resident_grid<TW, TH, 2 * NB, false>(k_blend_fwd<TW, TH, NB, false>, TW * TH / 2, b.total_tiles);
+    k_blend_fwd<TW, TH, NB, false><<<grid, TW * TH / 2, 0, st>>>(b, rec, pg, rg, o, order, ctr);
+  }
 }
 template <int TW, int TH>
 static bool launch_fwd_nb(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
