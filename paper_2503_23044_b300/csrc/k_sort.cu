@@ -355,36 +355,120 @@ cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
 }
 
 // ------------------------------------------------------------------ pair emission and tile ranges
-__global__ void __launch_bounds__(256) k_emit_pairs(const __grid_constant__ BatchDev b, const float4* __restrict__ rec,
-                                                    const uint32_t* __restrict__ counts,
-                                                    const uint32_t* __restrict__ sorted_g,
-                                                    const uint32_t* __restrict__ offs, const long long* __restrict__ d_ng,
-                                                    long long cap, int mode, long long n_explicit,
-                                                    const uint32_t* __restrict__ rows, uint32_t* __restrict__ tiles_out,
-                                                    uint32_t* __restrict__ g_out, uint32_t* err) {
+// Pair emission.  A warp takes 32 consecutive Gaussian-views in depth order;
+// their output runs are adjacent (offsets are an exclusive scan in that order),
+// so each lane writes its tiles into the warp's shared-memory window and the
+// warp then copies the window out with coalesced stores.  Pairs past the
+// window go to global memory directly.  A Gaussian with more than kEmitBig
+// pairs is emitted afterwards by the whole warp, one tile row per lane.
+constexpr int kEmitWarps = 4;
+constexpr int kEmitStage = 1024;   // staged pairs per warp
+constexpr uint32_t kEmitBig = 96;
+
+// write pair (tid, g) at output position o of a warp whose window starts at wbase
+__device__ __forceinline__ void emit_one(long long o, long long wbase, uint32_t tid, uint32_t g, long long cap,
+                                         uint32_t* s_t, uint32_t* s_g, uint32_t* __restrict__ tiles_out,
+                                         uint32_t* __restrict__ g_out) {
+  const long long rel = o - wbase;
+  if (rel < kEmitStage) {
+    s_t[rel] = tid;
+    s_g[rel] = g;
+  } else if (o < cap) {
+    tiles_out[o] = tid;
+    g_out[o] = g;
+  }
+}
+
+__global__ void __launch_bounds__(32 * kEmitWarps) k_emit_pairs(const __grid_constant__ BatchDev b,
+                                                                const float4* __restrict__ rec,
+                                                                const uint32_t* __restrict__ counts,
+                                                                const uint32_t* __restrict__ sorted_g,
+                                                                const uint32_t* __restrict__ offs,
+                                                                const long long* __restrict__ d_ng, long long cap,
+                                                                int mode, long long n_explicit,
+                                                                const uint32_t* __restrict__ rows,
+                                                                uint32_t* __restrict__ tiles_out,
+                                                                uint32_t* __restrict__ g_out, uint32_t* err) {
+  __shared__ uint32_t s_t[kEmitWarps][kEmitStage];
+  __shared__ uint32_t s_g[kEmitWarps][kEmitStage];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long ng = *d_ng;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < ng; k += (long long)gridDim.x * blockDim.x) {
-    const uint32_t g = sorted_g[k];
-    const uint32_t cnt = counts[g];
-    if (!cnt) continue;
-    const int vi = mode == PGS_MODE_EXPLICIT ? (int)(g / n_explicit) : (int)(rows[g / kNOff] >> 27);
-    const ViewDev& v = b.v[vi];
-    TileEllipse e;
-    const float4 r0 = rec[(long long)g * kRecF4], r1 = rec[(long long)g * kRecF4 + 1];
-    if (!tile_ellipse_setup(r0, r1, b.p, e)) continue;
-    long long o = offs[k];
-    const long long o_end = o + cnt;
-    const int tb = v.tile_base, tx_n = v.tiles_x;
-    for_each_tile_row(e, v, b.p.tile_w, b.p.tile_h, [&](int ty, int c0, int c1) {
-      for (int tx = c0; tx <= c1; ++tx) {
-        if (o < o_end && o < cap) {
-          tiles_out[o] = (uint32_t)(tb + ty * tx_n + tx);
-          g_out[o] = g;
-        }
-        ++o;
+  const long long stride = (long long)gridDim.x * kEmitWarps * 32;
+  for (long long kb = ((long long)blockIdx.x * kEmitWarps + w) * 32; kb < ng; kb += stride) {
+    const long long k = kb + lane;
+    const bool ok = k < ng;
+    uint32_t g = 0u, cnt = 0u;
+    long long o = 0;
+    if (ok) {
+      g = sorted_g[k];
+      cnt = counts[g];
+      o = offs[k];
+    }
+    const long long wbase = __shfl_sync(0xffffffffu, o, 0);   // lane 0 (k = kb < ng) starts the window
+    const long long o_beg = o, o_end = o + cnt;
+    const bool big = cnt > kEmitBig;
+    if (cnt && !big) {
+      const int vi = mode == PGS_MODE_EXPLICIT ? (int)(g / n_explicit) : (int)(rows[g / kNOff] >> 27);
+      const ViewDev& v = b.v[vi];
+      TileEllipse e;
+      const float4 r0 = rec[(long long)g * kRecF4], r1 = rec[(long long)g * kRecF4 + 1];
+      if (tile_ellipse_setup(r0, r1, b.p, e)) {
+        const int tb = v.tile_base, tx_n = v.tiles_x;
+        for_each_tile_row(e, v, b.p.tile_w, b.p.tile_h, [&](int ty, int c0, int c1) {
+          for (int tx = c0; tx <= c1; ++tx) {
+            if (o < o_end) emit_one(o, wbase, (uint32_t)(tb + ty * tx_n + tx), g, cap, s_t[w], s_g[w], tiles_out, g_out);
+            ++o;
+          }
+        });
       }
-    });
-    if (o != o_end) set_flag(err, kFlagCapacity);   // count and emit disagree: never expected
+      if (o != o_end) set_flag(err, kFlagCapacity);   // count and emit disagree: never expected
+    }
+    // large Gaussians: the warp takes them one at a time, lane l on tile rows ty0 + l, ty0 + l + 32, ...
+    unsigned bigs = __ballot_sync(0xffffffffu, ok && big);
+    while (bigs) {
+      const int src = __ffs(bigs) - 1;
+      bigs &= bigs - 1u;
+      const uint32_t gb = __shfl_sync(0xffffffffu, g, src);
+      const long long ob = __shfl_sync(0xffffffffu, o_beg, src), oe = __shfl_sync(0xffffffffu, o_end, src);
+      const int vi = mode == PGS_MODE_EXPLICIT ? (int)(gb / n_explicit) : (int)(rows[gb / kNOff] >> 27);
+      const ViewDev& v = b.v[vi];
+      TileEllipse e;
+      const float4 r0 = rec[(long long)gb * kRecF4], r1 = rec[(long long)gb * kRecF4 + 1];
+      const bool okb = tile_ellipse_setup(r0, r1, b.p, e);   // same record, same answer in every lane
+      long long pos = ob;
+      if (okb) {
+        const TileRows R = tile_rows(e, v, b.p.tile_w, b.p.tile_h);
+        const int tb = v.tile_base, tx_n = v.tiles_x;
+        for (int r0w = R.ty0; r0w <= R.ty1; r0w += 32) {   // warp-uniform bounds
+          const int ty = r0w + lane;
+          int c0 = 0, c1 = -1;
+          if (ty <= R.ty1 && !tile_row_span(e, v, b.p.tile_w, b.p.tile_h, R, ty, c0, c1)) c1 = c0 - 1;
+          const uint32_t rc = (uint32_t)max(0, c1 - c0 + 1);
+          uint32_t incl = rc;   // warp inclusive scan of the row counts
+#pragma unroll
+          for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+          }
+          long long q = pos + (incl - rc);
+          for (int tx = c0; tx <= c1; ++tx, ++q)
+            if (q < oe) emit_one(q, wbase, (uint32_t)(tb + ty * tx_n + tx), gb, cap, s_t[w], s_g[w], tiles_out, g_out);
+          pos += __shfl_sync(0xffffffffu, incl, 31);
+        }
+      }
+      if (lane == 0 && pos != oe) set_flag(err, kFlagCapacity);   // count and emit disagree: never expected
+    }
+    __syncwarp();
+    const uint32_t my_len = ok ? (uint32_t)(o_end - wbase) : 0u;
+    const uint32_t wlen = min(__reduce_max_sync(0xffffffffu, my_len), (uint32_t)kEmitStage);
+    for (uint32_t i = lane; i < wlen; i += 32) {
+      const long long p = wbase + i;
+      if (p < cap) {
+        tiles_out[p] = s_t[w][i];
+        g_out[p] = s_g[w][i];
+      }
+    }
+    __syncwarp();
   }
 }
 

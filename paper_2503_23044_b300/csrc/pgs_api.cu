@@ -426,7 +426,7 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
   prof_mark(s, PGS_STAGE_BIN, 0, st);
   launch_exclusive_scan(s->counts, s->gid_a, s->offs, s->d_tot + 1, d_G, s->scan_sums, st);
   k_pairs_total<<<1, 1, 0, st>>>(s->d_tot + 1, s->cap_pairs, d_P, s->d_flags);
-  k_emit_pairs<<<ns * 8, 256, 0, st>>>(b, s->rec, s->counts, s->gid_a, s->offs, d_G, s->cap_pairs, s->d.mode,
+  k_emit_pairs<<<ns * 16, 128, 0, st>>>(b, s->rec, s->counts, s->gid_a, s->offs, d_G, s->cap_pairs, s->d.mode,
                                        s->d.n_primitives, s->rows, s->ptile_a, s->pg_a, s->d_flags);
   s->launches += kScanLaunches + 2;
   prof_mark(s, PGS_STAGE_BIN, 1, st);

@@ -172,8 +172,15 @@ __device__ __forceinline__ float ellipse_x_at(const TileEllipse& e, float dy, fl
 
 // Visit the tiles of the ellipse in one view: for each tile row, the contiguous
 // column range [c0, c1] of touched tiles.  f(ty, c0, c1) is called per row.
-template <typename F>
-__device__ __forceinline__ void for_each_tile_row(const TileEllipse& e, const ViewDev& v, int TW, int TH, F f) {
+// Tile rows of an ellipse: the row range [ty0, ty1] and the dy of its left and
+// right extreme points; tile_row_span then gives one row's column range.
+// for_each_tile_row walks the rows in order; the pair emission also splits the
+// rows of large ellipses over a warp.  Both use the same per-row arithmetic.
+struct TileRows {
+  int ty0, ty1;
+  float dy_left, dy_right;
+};
+__device__ __forceinline__ TileRows tile_rows(const TileEllipse& e, const ViewDev& v, int TW, int TH) {
   const float cy = v.cy, cx = v.cx;
   float my_abs = __fadd_rn(__fadd_rn(e.myh, e.myl), cy);
   float y_lo = __fsub_rn(my_abs, e.ry), y_hi = __fadd_rn(my_abs, e.ry);
@@ -183,37 +190,53 @@ __device__ __forceinline__ void for_each_tile_row(const TileEllipse& e, const Vi
   // left / right extreme points of the ellipse occur at these dy
   float dy_left = __fdiv_rn(__fmul_rn(e.B, e.rx), e.C);
   float dy_right = -dy_left;
-  for (int ty = ty0; ty <= ty1; ++ty) {
-    int py0 = ty * TH, py1 = min(ty * TH + TH - 1, v.H - 1);
-    // band in dy relative to the mean (double-float mean): (y_rel - mh) - ml
-    float b0 = __fsub_rn(__fsub_rn(__fsub_rn((float)py0 + 0.5f, cy), e.myh), e.myl);
-    float b1 = __fsub_rn(__fsub_rn(__fsub_rn((float)py1 + 0.5f, cy), e.myh), e.myl);
-    if (b0 > e.ry || b1 < -e.ry) continue;
-    float c0 = fmaxf(b0, -e.ry), c1 = fminf(b1, e.ry);
-    float xmin = (dy_left >= c0 && dy_left <= c1) ? -e.rx : ellipse_x_at(e, dy_left < c0 ? c0 : c1, -1.f);
-    float xmax = (dy_right >= c0 && dy_right <= c1) ? e.rx : ellipse_x_at(e, dy_right < c0 ? c0 : c1, 1.f);
-    // tile column tx spans pixel centres [tx TW + 0.5, min(tx TW + TW - 1, W - 1) + 0.5]
-    // (relative: subtract cx); touched iff x0 - m <= xmax and x1 - m >= xmin
-    float ax_min = __fadd_rn(__fadd_rn(__fadd_rn(xmin, e.mxh), e.mxl), cx);
-    float ax_max = __fadd_rn(__fadd_rn(__fadd_rn(xmax, e.mxh), e.mxl), cx);
-    if (ax_min > (float)v.W - 0.5f || ax_max < 0.5f) continue;
-    // candidate range widened by one column each side, then tightened exactly
-    int tx0 = (int)clamp_tile(ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(ax_min, 0.5f), (float)TW), (float)TW))) - 1;
-    int tx1 = (int)clamp_tile(floorf(__fdiv_rn(__fsub_rn(ax_max, 0.5f), (float)TW))) + 1;
-    tx0 = max(tx0, 0);
-    tx1 = min(tx1, v.tiles_x - 1);
-    while (tx0 <= tx1) {
-      int px1 = min(tx0 * TW + TW - 1, v.W - 1);
-      float x1 = __fsub_rn(__fsub_rn(__fsub_rn((float)px1 + 0.5f, cx), e.mxh), e.mxl);
-      if (x1 >= xmin) break;
-      ++tx0;
-    }
-    while (tx1 >= tx0) {
-      float x0 = __fsub_rn(__fsub_rn(__fsub_rn((float)(tx1 * TW) + 0.5f, cx), e.mxh), e.mxl);
-      if (x0 <= xmax) break;
-      --tx1;
-    }
-    if (tx0 <= tx1) f(ty, tx0, tx1);
+  return TileRows{ty0, ty1, dy_left, dy_right};
+}
+
+__device__ __forceinline__ bool tile_row_span(const TileEllipse& e, const ViewDev& v, int TW, int TH,
+                                              const TileRows& R, int ty, int& tx0_out, int& tx1_out) {
+  const float cy = v.cy, cx = v.cx;
+  const float dy_left = R.dy_left, dy_right = R.dy_right;
+  int py0 = ty * TH, py1 = min(ty * TH + TH - 1, v.H - 1);
+  // band in dy relative to the mean (double-float mean): (y_rel - mh) - ml
+  float b0 = __fsub_rn(__fsub_rn(__fsub_rn((float)py0 + 0.5f, cy), e.myh), e.myl);
+  float b1 = __fsub_rn(__fsub_rn(__fsub_rn((float)py1 + 0.5f, cy), e.myh), e.myl);
+  if (b0 > e.ry || b1 < -e.ry) return false;
+  float c0 = fmaxf(b0, -e.ry), c1 = fminf(b1, e.ry);
+  float xmin = (dy_left >= c0 && dy_left <= c1) ? -e.rx : ellipse_x_at(e, dy_left < c0 ? c0 : c1, -1.f);
+  float xmax = (dy_right >= c0 && dy_right <= c1) ? e.rx : ellipse_x_at(e, dy_right < c0 ? c0 : c1, 1.f);
+  // tile column tx spans pixel centres [tx TW + 0.5, min(tx TW + TW - 1, W - 1) + 0.5]
+  // (relative: subtract cx); touched iff x0 - m <= xmax and x1 - m >= xmin
+  float ax_min = __fadd_rn(__fadd_rn(__fadd_rn(xmin, e.mxh), e.mxl), cx);
+  float ax_max = __fadd_rn(__fadd_rn(__fadd_rn(xmax, e.mxh), e.mxl), cx);
+  if (ax_min > (float)v.W - 0.5f || ax_max < 0.5f) return false;
+  // candidate range widened by one column each side, then tightened exactly
+  int tx0 = (int)clamp_tile(ceilf(__fdiv_rn(__fsub_rn(__fadd_rn(ax_min, 0.5f), (float)TW), (float)TW))) - 1;
+  int tx1 = (int)clamp_tile(floorf(__fdiv_rn(__fsub_rn(ax_max, 0.5f), (float)TW))) + 1;
+  tx0 = max(tx0, 0);
+  tx1 = min(tx1, v.tiles_x - 1);
+  while (tx0 <= tx1) {
+    int px1 = min(tx0 * TW + TW - 1, v.W - 1);
+    float x1 = __fsub_rn(__fsub_rn(__fsub_rn((float)px1 + 0.5f, cx), e.mxh), e.mxl);
+    if (x1 >= xmin) break;
+    ++tx0;
+  }
+  while (tx1 >= tx0) {
+    float x0 = __fsub_rn(__fsub_rn(__fsub_rn((float)(tx1 * TW) + 0.5f, cx), e.mxh), e.mxl);
+    if (x0 <= xmax) break;
+    --tx1;
+  }
+  tx0_out = tx0;
+  tx1_out = tx1;
+  return tx0 <= tx1;
+}
+
+template <typename F>
+__device__ __forceinline__ void for_each_tile_row(const TileEllipse& e, const ViewDev& v, int TW, int TH, F f) {
+  const TileRows R = tile_rows(e, v, TW, TH);
+  for (int ty = R.ty0; ty <= R.ty1; ++ty) {
+    int tx0, tx1;
+    if (tile_row_span(e, v, TW, TH, R, ty, tx0, tx1)) f(ty, tx0, tx1);
   }
 }
 
