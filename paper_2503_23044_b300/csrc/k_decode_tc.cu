@@ -133,32 +133,40 @@ __host__ __device__ inline int perm_out(int n) {
 
 using namespace tc;
 
-__global__ void __launch_bounds__(128) k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A,
+// 256 threads: warps 0-3 own rows 0-127 of a tile for the operands and layer 1
+// (warp w reads TMEM lanes 32 w .. 32 w + 31); after layer 2, warps w and w + 4
+// share those 32 rows, taking Gaussians 0-4 and 5-9 of each row.
+constexpr int kTcThreads = 256;
+
+__global__ void __launch_bounds__(kTcThreads) k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A,
                                                            pgs_mlp_ptrs Wt, const uint32_t* __restrict__ rows,
                                                            const long long* __restrict__ n_rows_p, long long cap,
                                                            float4* __restrict__ rec, uint32_t* __restrict__ counts,
                                                            uint32_t* __restrict__ keys, DecodeOut dec, uint32_t* err) {
   __shared__ __align__(1024) Smem sm;
   const int tid = threadIdx.x, warp = tid >> 5;
+  const bool row_thread = tid < kRows;                // operand rows and layer 1
+  const int erow = (warp & 3) * 32 + (tid & 31);      // the row whose Gaussians this thread projects
+  const int ehalf = warp >> 2;                        // Gaussians 5 * ehalf .. 5 * ehalf + 4
   const int in_dim = b.p.in_dim;
   char* A1b = reinterpret_cast<char*>(sm.A1);
   char* B1b = reinterpret_cast<char*>(sm.B1);
   char* A2b = reinterpret_cast<char*>(sm.A2);
   char* B2b = reinterpret_cast<char*>(sm.B2);
   // decoder weights -> BF16 operand tiles (zero padded); biases stay FP32 for the epilogue
-  for (int t = tid; t < kN1 * kK1; t += 128) {
+  for (int t = tid; t < kN1 * kK1; t += kTcThreads) {
     const int n = t / kK1, k = t % kK1;
     const float w = k < in_dim ? Wt.W1[n * in_dim + k] : 0.f;
     *reinterpret_cast<__nv_bfloat16*>(B1b + kmaj_off(n, k, kK1)) = __float2bfloat16_rn(w);
   }
-  for (int t = tid; t < kN2 * kK2; t += 128) {
+  for (int t = tid; t < kN2 * kK2; t += kTcThreads) {
     const int n = t / kK2, k = t % kK2;
     const int o = perm_out(n);
     const float w = o >= 0 ? Wt.W2[o * kHidden + k] : 0.f;
     *reinterpret_cast<__nv_bfloat16*>(B2b + kmaj_off(n, k, kK2)) = __float2bfloat16_rn(w);
   }
   if (tid < kN1) sm.b1[tid] = Wt.b1[tid];
-  for (int t = tid; t < kN2; t += 128) {
+  for (int t = tid; t < kN2; t += kTcThreads) {
     const int o = perm_out(t);
     sm.b2p[t] = o >= 0 ? Wt.b2[o] : 0.f;
   }
@@ -178,7 +186,7 @@ __global__ void __launch_bounds__(128) k_decode_project_tc(const __grid_constant
   __syncthreads();
   fence_after();
   const uint32_t tmem = sm.tmem_base;
-  const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+  const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
   const uint32_t a1 = smem_u32(sm.A1), b1s = smem_u32(sm.B1), a2 = smem_u32(sm.A2), b2s = smem_u32(sm.B2);
   constexpr uint32_t kIdesc1 = make_idesc(kRows, kN1), kIdesc2 = make_idesc(kRows, kN2);
   const long long n_rows = min(*n_rows_p, cap);
@@ -186,25 +194,22 @@ __global__ void __launch_bounds__(128) k_decode_project_tc(const __grid_constant
   uint32_t phase = 0;
   bool timed_out = false;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const long long r = tile * kRows + tid;
-    const bool valid = r < n_rows;
-    int vi = 0;
-    long long a = 0;
-    float X[kMaxIn];
+    if (row_thread) {
+      const long long r = tile * kRows + tid;
+      float X[kMaxIn];
 #pragma unroll
-    for (int k = 0; k < kMaxIn; ++k) X[k] = 0.f;
-    if (valid) {
-      const uint32_t rw = rows[r];
-      vi = rw >> 27;
-      a = rw & ((1u << 27) - 1);
-      decoder_input(A, b.v[vi], a, in_dim, X);
-    }
-    // layer-1 operand row (BF16, zero padded to K = 48)
+      for (int k = 0; k < kMaxIn; ++k) X[k] = 0.f;
+      if (r < n_rows) {
+        const uint32_t rw = rows[r];
+        decoder_input(A, b.v[rw >> 27], rw & ((1u << 27) - 1), in_dim, X);
+      }
+      // layer-1 operand row (BF16, zero padded to K = 48)
 #pragma unroll
-    for (int k = 0; k < kK1; k += 2) {
-      const float x0 = (k < kMaxIn && k < in_dim) ? X[k < kMaxIn ? k : 0] : 0.f;
-      const float x1 = (k + 1 < kMaxIn && k + 1 < in_dim) ? X[k + 1 < kMaxIn ? k + 1 : 0] : 0.f;
-      *reinterpret_cast<__nv_bfloat162*>(A1b + kmaj_off(tid, k, kK1)) = __floats2bfloat162_rn(x0, x1);
+      for (int k = 0; k < kK1; k += 2) {
+        const float x0 = (k < kMaxIn && k < in_dim) ? X[k < kMaxIn ? k : 0] : 0.f;
+        const float x1 = (k + 1 < kMaxIn && k + 1 < in_dim) ? X[k + 1 < kMaxIn ? k + 1 : 0] : 0.f;
+        *reinterpret_cast<__nv_bfloat162*>(A1b + kmaj_off(tid, k, kK1)) = __floats2bfloat162_rn(x0, x1);
+      }
     }
     fence_async_smem();
     fence_before();
@@ -220,13 +225,15 @@ __global__ void __launch_bounds__(128) k_decode_project_tc(const __grid_constant
     if (!__syncthreads_and(mbar_wait(mbar, phase))) { timed_out = true; break; }
     phase ^= 1u;
     fence_after();
-    float h[32];
-    tmem_ld32(tmem + lane_base, h);
-    // hidden layer: ReLU(D1 + b1) -> layer-2 operand row (BF16)
+    if (row_thread) {
+      float h[32];
+      tmem_ld32(tmem + lane_base, h);
+      // hidden layer: ReLU(D1 + b1) -> layer-2 operand row (BF16)
 #pragma unroll
-    for (int k = 0; k < kK2; k += 2) {
-      const float h0 = fmaxf(h[k] + sm.b1[k], 0.f), h1 = fmaxf(h[k + 1] + sm.b1[k + 1], 0.f);
-      *reinterpret_cast<__nv_bfloat162*>(A2b + kmaj_off(tid, k, kK2)) = __floats2bfloat162_rn(h0, h1);
+      for (int k = 0; k < kK2; k += 2) {
+        const float h0 = fmaxf(h[k] + sm.b1[k], 0.f), h1 = fmaxf(h[k + 1] + sm.b1[k + 1], 0.f);
+        *reinterpret_cast<__nv_bfloat162*>(A2b + kmaj_off(tid, k, kK2)) = __floats2bfloat162_rn(h0, h1);
+      }
     }
     fence_async_smem();
     fence_before();
@@ -242,19 +249,29 @@ __global__ void __launch_bounds__(128) k_decode_project_tc(const __grid_constant
     if (!__syncthreads_and(mbar_wait(mbar, phase))) { timed_out = true; break; }
     phase ^= 1u;
     fence_after();
+    // epilogue: this thread's row, Gaussians 5 ehalf .. 5 ehalf + 4 (column groups of two Gaussians)
+    const long long r = tile * kRows + erow;
+    const bool valid = r < n_rows;
+    int vi = 0;
+    long long a = 0;
     float l[3] = {1.f, 1.f, 1.f}, xa[3] = {0.f, 0.f, 0.f};
     if (valid) {
+      const uint32_t rw = rows[r];
+      vi = rw >> 27;
+      a = rw & ((1u << 27) - 1);
       l[0] = expf(A.log_l[3 * a]); l[1] = expf(A.log_l[3 * a + 1]); l[2] = expf(A.log_l[3 * a + 2]);
       xa[0] = A.x[3 * a]; xa[1] = A.x[3 * a + 1]; xa[2] = A.x[3 * a + 2];
     }
+    const int j_lo = 5 * ehalf, j_hi = j_lo + 5;
 #pragma unroll 1
-    for (int grp = 0; grp < kN2 / kGroupCols; ++grp) {
+    for (int grp = j_lo / 2; grp <= (j_hi - 1) / 2; ++grp) {
       float zc[32];
       tmem_ld32(tmem + lane_base + kD2Col + grp * kGroupCols, zc);
       if (valid) {
 #pragma unroll
         for (int u = 0; u < 2; ++u) {
           const int j = 2 * grp + u;
+          if (j < j_lo || j >= j_hi) continue;
           float z[kPerGauss];
 #pragma unroll
           for (int t = 0; t < kPerGauss; ++t) z[t] = zc[kPerGauss * u + t] + sm.b2p[grp * kGroupCols + kPerGauss * u + t];
