@@ -133,10 +133,11 @@ __host__ __device__ inline int perm_out(int n) {
 
 using namespace tc;
 
-// 256 threads: warps 0-3 own rows 0-127 of a tile for the operands and layer 1
-// (warp w reads TMEM lanes 32 w .. 32 w + 31); after layer 2, warps w and w + 4
-// share those 32 rows, taking Gaussians 0-4 and 5-9 of each row.
-constexpr int kTcThreads = 256;
+// 384 threads: warps 0-3 own rows 0-127 of a tile for the operands and layer 1
+// (warp w reads TMEM lanes 32 (w mod 4) .. + 31); after layer 2, warps w, w + 4
+// and w + 8 share those 32 rows, taking Gaussians 0-3, 4-6 and 7-9 of each row.
+constexpr int kTcThreads = 384;
+__device__ __forceinline__ int epi_first(int part) { return part == 0 ? 0 : (part == 1 ? 4 : 7); }
 
 __global__ void __launch_bounds__(kTcThreads) k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A,
                                                            pgs_mlp_ptrs Wt, const uint32_t* __restrict__ rows,
@@ -147,7 +148,7 @@ __global__ void __launch_bounds__(kTcThreads) k_decode_project_tc(const __grid_c
   const int tid = threadIdx.x, warp = tid >> 5;
   const bool row_thread = tid < kRows;                // operand rows and layer 1
   const int erow = (warp & 3) * 32 + (tid & 31);      // the row whose Gaussians this thread projects
-  const int ehalf = warp >> 2;                        // Gaussians 5 * ehalf .. 5 * ehalf + 4
+  const int epart = warp >> 2;                        // Gaussians epi_first(epart) .. epi_first(epart + 1) - 1
   const int in_dim = b.p.in_dim;
   char* A1b = reinterpret_cast<char*>(sm.A1);
   char* B1b = reinterpret_cast<char*>(sm.B1);
@@ -249,7 +250,7 @@ __global__ void __launch_bounds__(kTcThreads) k_decode_project_tc(const __grid_c
     if (!__syncthreads_and(mbar_wait(mbar, phase))) { timed_out = true; break; }
     phase ^= 1u;
     fence_after();
-    // epilogue: this thread's row, Gaussians 5 ehalf .. 5 ehalf + 4 (column groups of two Gaussians)
+    // epilogue: this thread's row and part of its Gaussians (column groups of two Gaussians)
     const long long r = tile * kRows + erow;
     const bool valid = r < n_rows;
     int vi = 0;
@@ -262,7 +263,7 @@ __global__ void __launch_bounds__(kTcThreads) k_decode_project_tc(const __grid_c
       l[0] = expf(A.log_l[3 * a]); l[1] = expf(A.log_l[3 * a + 1]); l[2] = expf(A.log_l[3 * a + 2]);
       xa[0] = A.x[3 * a]; xa[1] = A.x[3 * a + 1]; xa[2] = A.x[3 * a + 2];
     }
-    const int j_lo = 5 * ehalf, j_hi = j_lo + 5;
+    const int j_lo = epi_first(epart), j_hi = epart == 2 ? kNOff : epi_first(epart + 1);
 #pragma unroll 1
     for (int grp = j_lo / 2; grp <= (j_hi - 1) / 2; ++grp) {
       float zc[32];

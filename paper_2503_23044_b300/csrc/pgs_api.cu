@@ -366,7 +366,7 @@ pgs_status run_project(pgs_scene* s, const BatchDev& b, DecodeOut dec, bool proj
     k_rows_total<<<1, 1, 0, st>>>(s->d_tot, s->cap_rows, s->d_cnt, s->d_cnt + 1, s->d_flags);
     if (s->d.params.decode_precision == PGS_DECODE_BF16) {
       const int grid = (int)std::max<long long>(1, std::min<long long>((s->cap_rows + 127) / 128, 2ll * ns));
-      k_decode_project_tc<<<grid, 256, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
+      k_decode_project_tc<<<grid, 384, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
                                                 project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags);
     } else {
       k_decode_project<<<ns * 4, 256, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
