@@ -211,6 +211,154 @@ __global__ void __launch_bounds__(256, 3) k_loss_grad(const __grid_constant__ Ba
   if (threadIdx.x < 3) partials[blockIdx.x * 3 + threadIdx.x] = s_red[threadIdx.x][0];
 }
 
+// ---------------------------------------------------------------- quad form
+// When every view's width is a multiple of 4 and every map is 16-byte aligned,
+// a thread takes 4 consecutive pixels of one row: each map is read and written
+// with one 16-byte access per quad; the stencil's vertical neighbours come as
+// two more 16-byte loads and the horizontal ones as two scalars.  The per-pixel
+// arithmetic is the scalar form's (normal_valid and the loss terms below).
+__device__ __forceinline__ float4 ld4(const float* __restrict__ p) { return __ldg(reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ float f4(const float4& v, int i) { return i == 0 ? v.x : (i == 1 ? v.y : (i == 2 ? v.z : v.w)); }
+__device__ __forceinline__ void set4(float4& v, int i, float x) {
+  if (i == 0) v.x = x; else if (i == 1) v.y = x; else if (i == 2) v.z = x; else v.w = x;
+}
+
+__device__ __forceinline__ void load_quad(const BatchDev& b, long long p, int& vh, const float* __restrict__ depth,
+                                          const float* __restrict__ normal, const float* __restrict__ mask,
+                                          PixIn (&I)[4]) {
+  const PixCtx c = pix_ctx(b, p, vh);
+  const ViewDev& v = b.v[c.v];
+  const float4 d = ld4(depth + p);
+  const bool rowin = c.py >= 1 && c.py <= v.H - 2;
+  float4 up = make_float4(0.f, 0.f, 0.f, 0.f), dn = up;
+  if (rowin) { up = ld4(depth + p - v.W); dn = ld4(depth + p + v.W); }
+  const float left = c.px >= 1 ? __ldg(depth + p - 1) : 0.f;
+  const float right = c.px + 4 <= v.W - 1 ? __ldg(depth + p + 4) : 0.f;
+  const float4 n0 = ld4(normal + c.p3), n1 = ld4(normal + c.p3 + c.HW), n2 = ld4(normal + c.p3 + 2 * c.HW);
+  const float4 m = ld4(mask + p);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    I[i].c = c;
+    I[i].c.px = c.px + i;
+    I[i].c.p = c.p + i;
+    I[i].c.p3 = c.p3 + i;
+    I[i].inter = rowin && c.px + i >= 1 && c.px + i <= v.W - 2;
+    I[i].d0 = f4(d, i);
+    I[i].dl = i == 0 ? left : f4(d, i - 1);
+    I[i].dr = i == 3 ? right : f4(d, i + 1);
+    I[i].du = f4(up, i);
+    I[i].dd = f4(dn, i);
+    I[i].N[0] = f4(n0, i); I[i].N[1] = f4(n1, i); I[i].N[2] = f4(n2, i);
+    I[i].mask = f4(m, i);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_loss_counts4(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
+                                                      pgs_target_ptrs tgt, uint32_t* __restrict__ counts) {
+  __shared__ uint32_t s_cnt[kMaxViews][2];
+  for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x) (&s_cnt[0][0])[i] = 0;
+  __syncthreads();
+  long long s, e;
+  range_of_block(b.total_pixels / 4, s, e);
+  int vh = s < e ? view_of_pixel(b, 4 * s) : 0;
+  for (long long q0 = s + threadIdx.x; q0 < e; q0 += 2 * (long long)blockDim.x) {
+    PixIn I[2][4];
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      const long long q = q0 + u * (long long)blockDim.x;
+      if (q < e) load_quad(b, 4 * q, vh, img.depth, img.normal, tgt.mask, I[u]);
+    }
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+      if (q0 + u * (long long)blockDim.x >= e) break;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        float nd[3], nn;
+        if (I[u][i].mask > 0.f) atomicAdd(&s_cnt[I[u][i].c.v][0], 1u);
+        if (normal_valid(b, I[u][i], nd, nn)) atomicAdd(&s_cnt[I[u][i].c.v][1], 1u);
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x)
+    if ((&s_cnt[0][0])[i]) atomicAdd(counts + i, (&s_cnt[0][0])[i]);
+}
+
+__global__ void __launch_bounds__(256) k_loss_grad4(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
+                                                    pgs_target_ptrs tgt, pgs_loss_params lp,
+                                                    const uint32_t* __restrict__ counts, pgs_image_grad_ptrs g,
+                                                    float* __restrict__ partials, uint32_t* err) {
+  __shared__ float s_red[3][256];
+  long long s, e;
+  range_of_block(b.total_pixels / 4, s, e);
+  const float invB = 1.f / (float)b.n_views;
+  float l_rgb = 0.f, l_d = 0.f, l_n = 0.f;
+  bool bad = false;
+  int vh = s < e ? view_of_pixel(b, 4 * s) : 0;
+  for (long long q = s + threadIdx.x; q < e; q += blockDim.x) {
+    const long long p = 4 * q;
+    PixIn I[4];
+    load_quad(b, p, vh, img.depth, img.normal, tgt.mask, I);
+    const PixCtx& c = I[0].c;
+    float4 c3[3], t3[3];
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      c3[ch] = ld4(img.rgb + c.p3 + ch * c.HW);
+      t3[ch] = ld4(tgt.rgb + c.p3 + ch * c.HW);
+    }
+    const float4 pr = ld4(tgt.prior + p);
+    const float k_rgb = invB / (3.f * (float)c.HW);
+    const float kd = lp.lambda_depth * invB / fmaxf(1.f, (float)counts[2 * c.v]);
+    const float kn = lp.lambda_normal * invB / fmaxf(1.f, (float)counts[2 * c.v + 1]);
+    float4 grgb[3], gdep, gnor[3];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+      for (int ch = 0; ch < 3; ++ch) {
+        const float d = f4(c3[ch], i) - f4(t3[ch], i);
+        l_rgb += fabsf(d) * k_rgb;
+        set4(grgb[ch], i, sgnf(d) * k_rgb);
+      }
+      const PixIn& P = I[i];
+      float gd = 0.f;
+      if (P.mask > 0.f) {
+        const float d = P.d0 - f4(pr, i);
+        l_d += P.mask * fabsf(d) * kd;
+        gd = P.mask * sgnf(d) * kd;
+      }
+      set4(gdep, i, gd);
+      float nd[3], nn, gn0 = 0.f, gn1 = 0.f, gn2 = 0.f;
+      if (normal_valid(b, P, nd, nn)) {
+        const float inn = 1.f / nn;
+        const float cosang = (nd[0] * P.N[0] + nd[1] * P.N[1] + nd[2] * P.N[2]) * inn;
+        l_n += (1.f - cosang) * kn;
+        gn0 = -kn * (nd[0] * inn - cosang * P.N[0] * inn * inn);
+        gn1 = -kn * (nd[1] * inn - cosang * P.N[1] * inn * inn);
+        gn2 = -kn * (nd[2] * inn - cosang * P.N[2] * inn * inn);
+      }
+      set4(gnor[0], i, gn0); set4(gnor[1], i, gn1); set4(gnor[2], i, gn2);
+      bad |= !isfinite(gd) || !isfinite(gn0) || !isfinite(gn1) || !isfinite(gn2);
+    }
+#pragma unroll
+    for (int ch = 0; ch < 3; ++ch) {
+      *reinterpret_cast<float4*>(g.rgb + c.p3 + ch * c.HW) = grgb[ch];
+      *reinterpret_cast<float4*>(g.normal + c.p3 + ch * c.HW) = gnor[ch];
+    }
+    *reinterpret_cast<float4*>(g.depth + p) = gdep;
+  }
+  if (bad) set_flag(err, kFlagNonfinite);
+  s_red[0][threadIdx.x] = l_rgb;
+  s_red[1][threadIdx.x] = l_d;
+  s_red[2][threadIdx.x] = l_n;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if ((int)threadIdx.x < o)
+      for (int t = 0; t < 3; ++t) s_red[t][threadIdx.x] += s_red[t][threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x < 3) partials[blockIdx.x * 3 + threadIdx.x] = s_red[threadIdx.x][0];
+}
+
 __global__ void __launch_bounds__(256) k_loss_final(const float* __restrict__ partials, int nb, float* __restrict__ loss,
                                                     uint32_t* err) {
   __shared__ float s_red[3][256];
@@ -238,8 +386,19 @@ void launch_loss(const BatchDev& b, const pgs_image_ptrs& img, const pgs_target_
                  float* loss, const pgs_image_grad_ptrs& g, uint32_t* counts, float* partials, uint32_t* err,
                  cudaStream_t st) {
   cudaMemsetAsync(counts, 0, kMaxViews * 2 * sizeof(uint32_t), st);
-  k_loss_counts<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, counts);
-  k_loss_grad<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, lp, counts, g, partials, err);
+  bool quad = true;
+  for (int v = 0; v < b.n_views; ++v) quad = quad && b.v[v].W % 4 == 0;
+  for (const void* ptr : {(const void*)img.rgb, (const void*)img.depth, (const void*)img.normal, (const void*)tgt.rgb,
+                          (const void*)tgt.prior, (const void*)tgt.mask, (const void*)g.rgb, (const void*)g.depth,
+                          (const void*)g.normal})
+    quad = quad && (reinterpret_cast<uintptr_t>(ptr) & 15u) == 0;
+  if (quad) {
+    k_loss_counts4<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, counts);
+    k_loss_grad4<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, lp, counts, g, partials, err);
+  } else {
+    k_loss_counts<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, counts);
+    k_loss_grad<<<kLossBlocks, 256, 0, st>>>(b, img, tgt, lp, counts, g, partials, err);
+  }
   k_loss_final<<<1, 256, 0, st>>>(partials, kLossBlocks, loss, err);
 }
 

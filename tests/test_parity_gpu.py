@@ -181,8 +181,13 @@ def test_empty_scene_and_capacity_overflow():
 
 
 # ------------------------------------------------------------------ loss
-def test_loss_matches_oracle():
-    cams = [synth.identity_camera(40, 30, 40.0), synth.identity_camera(23, 17, 20.0)]
+@pytest.mark.parametrize("sizes", [((40, 30), (23, 17)), ((40, 30), (24, 16))],
+                         ids=["scalar-form (width 23)", "quad-form (widths % 4 == 0)"])
+def test_loss_matches_oracle(sizes):
+    """Both loss forms: per pixel when a width is not a multiple of 4, four
+    pixels per thread with 16-byte accesses otherwise."""
+    (w0, h0), (w1, h1) = sizes
+    cams = [synth.identity_camera(w0, h0, 40.0), synth.identity_camera(w1, h1, 20.0)]
     maps = synth.random_maps(cams, seed=7)
     tv = synth.random_maps(cams, seed=8)
     gen = torch.Generator().manual_seed(9)
