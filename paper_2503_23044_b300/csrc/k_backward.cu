@@ -185,13 +185,42 @@ __global__ void __launch_bounds__(128) k_project_bwd_explicit(const __grid_const
 }
 
 // ---------------------------------------------------------------- anchor mode
-struct MlpSmemB {
-  float W1[kHidden][kMaxIn];
+struct __align__(16) MlpSmemB {
+  float W1[kHidden][kMaxIn];   // zero past in_dim; rows are 16-byte aligned (36 floats)
   float b1[kHidden];
-  float W2[kOut][kHidden];
+  float W2[kOut][kHidden];     // rows of 32 floats
   float b2[kOut];
 };
+static_assert(kMaxIn % 4 == 0 && kHidden % 4 == 0, "float4 rows");
 
+// z = b2[o] + W2[o] . H (one decoder output, weight row read as float4)
+__device__ __forceinline__ float w2_dot(const MlpSmemB& m, int o, const float (&H)[kHidden]) {
+  const float4* w = reinterpret_cast<const float4*>(m.W2[o]);
+  float acc = m.b2[o];
+#pragma unroll
+  for (int q = 0; q < kHidden / 4; ++q) {
+    const float4 ww = w[q];
+    acc = fmaf(ww.x, H[4 * q], acc); acc = fmaf(ww.y, H[4 * q + 1], acc);
+    acc = fmaf(ww.z, H[4 * q + 2], acc); acc = fmaf(ww.w, H[4 * q + 3], acc);
+  }
+  return acc;
+}
+// dH += W2[o]^T dz (one decoder output's contribution to the hidden-layer gradient)
+__device__ __forceinline__ void w2_axpy(const MlpSmemB& m, int o, float dz, float (&dH)[kHidden]) {
+  const float4* w = reinterpret_cast<const float4*>(m.W2[o]);
+#pragma unroll
+  for (int q = 0; q < kHidden / 4; ++q) {
+    const float4 ww = w[q];
+    dH[4 * q] = fmaf(ww.x, dz, dH[4 * q]); dH[4 * q + 1] = fmaf(ww.y, dz, dH[4 * q + 1]);
+    dH[4 * q + 2] = fmaf(ww.z, dz, dH[4 * q + 2]); dH[4 * q + 3] = fmaf(ww.w, dz, dH[4 * q + 3]);
+  }
+}
+
+// Per visible row: recompute the decoder forward (H, then each Gaussian's 11
+// outputs), run the projection backward of its 10 Gaussians, and carry the
+// gradient back through the decoder: dZ (11 entries per Gaussian, written to
+// the weight-gradient scratch as they are formed), dH accumulated in registers
+// Gaussian by Gaussian, dX = W1^T (dH . [H > 0]).
 __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A,
                                                     pgs_mlp_ptrs Wt, const uint32_t* __restrict__ rows,
                                                     const long long* __restrict__ n_rows_p, long long cap,
@@ -200,7 +229,10 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
                                                     float* __restrict__ sc_dH, float* __restrict__ sc_X, uint32_t* err) {
   __shared__ MlpSmemB m;
   const int in_dim = b.p.in_dim;
-  for (int t = threadIdx.x; t < kHidden * in_dim; t += blockDim.x) m.W1[t / in_dim][t % in_dim] = Wt.W1[t];
+  for (int t = threadIdx.x; t < kHidden * kMaxIn; t += blockDim.x) {
+    const int i = t / kMaxIn, j = t % kMaxIn;
+    m.W1[i][j] = j < in_dim ? Wt.W1[i * in_dim + j] : 0.f;
+  }
   for (int t = threadIdx.x; t < kHidden; t += blockDim.x) m.b1[t] = Wt.b1[t];
   for (int t = threadIdx.x; t < kOut * kHidden; t += blockDim.x) m.W2[t / kHidden][t % kHidden] = Wt.W2[t];
   for (int t = threadIdx.x; t < kOut; t += blockDim.x) m.b2[t] = Wt.b2[t];
@@ -212,37 +244,59 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
     const int vi = rw >> 27;
     const long long a = rw & ((1u << 27) - 1);
     const ViewDev& v = b.v[vi];
-    float X[kMaxIn];
-    const float ddx = A.x[3 * a] - v.center[0], ddy = A.x[3 * a + 1] - v.center[1], ddz = A.x[3 * a + 2] - v.center[2];
-    const float dist = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz), idist = 1.f / dist;
-    for (int j = 0; j < kFeat; ++j) X[j] = A.feat[a * kFeat + j];
-    X[32] = ddx * idist; X[33] = ddy * idist; X[34] = ddz * idist;
-    if (in_dim == 36) X[35] = dist;
     float H[kHidden];
-    for (int i = 0; i < kHidden; ++i) {
-      float acc = m.b1[i];
-      for (int j = 0; j < in_dim; ++j) acc = fmaf(m.W1[i][j], X[j], acc);
-      H[i] = fmaxf(acc, 0.f);
+    float dir0, dir1, dir2, idist;
+    {
+      float X[kMaxIn];
+      const float ddx = A.x[3 * a] - v.center[0], ddy = A.x[3 * a + 1] - v.center[1], ddz = A.x[3 * a + 2] - v.center[2];
+      const float dist = sqrtf(ddx * ddx + ddy * ddy + ddz * ddz);
+      idist = 1.f / dist;
+#pragma unroll
+      for (int j = 0; j < kFeat; ++j) X[j] = A.feat[a * kFeat + j];
+      dir0 = ddx * idist; dir1 = ddy * idist; dir2 = ddz * idist;
+      X[32] = dir0; X[33] = dir1; X[34] = dir2;
+      X[35] = in_dim == 36 ? dist : 0.f;
+#pragma unroll
+      for (int i = 0; i < kHidden; ++i) {
+        const float4* w = reinterpret_cast<const float4*>(m.W1[i]);
+        float acc = m.b1[i];
+#pragma unroll
+        for (int q = 0; q < kMaxIn / 4; ++q) {
+          const float4 ww = w[q];
+          acc = fmaf(ww.x, X[4 * q], acc); acc = fmaf(ww.y, X[4 * q + 1], acc);
+          acc = fmaf(ww.z, X[4 * q + 2], acc); acc = fmaf(ww.w, X[4 * q + 3], acc);
+        }
+        H[i] = fmaxf(acc, 0.f);
+      }
+      // row scratch for the weight gradients, in 32-row blocks (sc_at)
+#pragma unroll
+      for (int j = 0; j < kMaxIn; ++j)
+        if (j < in_dim) sc_X[sc_at(r, j, kMaxIn)] = X[j];
     }
+#pragma unroll
+    for (int h = 0; h < kHidden; ++h) sc_H[sc_at(r, h, kHidden)] = H[h];
     const float l[3] = {expf(A.log_l[3 * a]), expf(A.log_l[3 * a + 1]), expf(A.log_l[3 * a + 2])};
     const float xa[3] = {A.x[3 * a], A.x[3 * a + 1], A.x[3 * a + 2]};
-    float dZ[kOut];
-    for (int t = 0; t < kOut; ++t) dZ[t] = 0.f;
+    float dH[kHidden];
+#pragma unroll
+    for (int h = 0; h < kHidden; ++h) dH[h] = 0.f;
     float dl[3] = {0.f, 0.f, 0.f}, dxa[3] = {0.f, 0.f, 0.f};
     bool any = false, bad = false;
 #pragma unroll 1
     for (int j = 0; j < kNOff; ++j) {
-      float gr[13];
-      if (!load_grad(grad, r * kNOff + j, gr)) continue;
-      any = true;
       const int idx[11] = {j, 10 + 3 * j, 11 + 3 * j, 12 + 3 * j, 40 + 3 * j, 41 + 3 * j, 42 + 3 * j,
                            70 + 4 * j, 71 + 4 * j, 72 + 4 * j, 73 + 4 * j};
-      float z[11];
-      for (int t = 0; t < 11; ++t) {
-        float acc = m.b2[idx[t]];
-        for (int h = 0; h < kHidden; ++h) acc = fmaf(m.W2[idx[t]][h], H[h], acc);
-        z[t] = acc;
+      float dz[11];
+      float gr[13];
+      if (!load_grad(grad, r * kNOff + j, gr)) {
+#pragma unroll
+        for (int t = 0; t < 11; ++t) sc_dZ[sc_at(r, idx[t], kOut)] = 0.f;
+        continue;
       }
+      any = true;
+      float z[11];
+#pragma unroll
+      for (int t = 0; t < 11; ++t) z[t] = w2_dot(m, idx[t], H);
       const float op = sigm(z[0]);
       const float col[3] = {sigm(z[1]), sigm(z[2]), sigm(z[3])};
       const float sgs[3] = {sigm(z[4]), sigm(z[5]), sigm(z[6])};
@@ -257,50 +311,60 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
       project_backward(b, v, mu, s, q, gr, pg);
       float dq[4];
       quat_norm_backward(qr, qn, pg.dq, dq);
-      dZ[idx[0]] = pg.dop * op * (1.f - op);
+      dz[0] = pg.dop * op * (1.f - op);
+#pragma unroll
       for (int t = 0; t < 3; ++t) {
-        dZ[idx[1 + t]] = pg.dcol[t] * col[t] * (1.f - col[t]);
-        dZ[idx[4 + t]] = pg.ds[t] * l[t] * sgs[t] * (1.f - sgs[t]);
+        dz[1 + t] = pg.dcol[t] * col[t] * (1.f - col[t]);
+        dz[4 + t] = pg.ds[t] * l[t] * sgs[t] * (1.f - sgs[t]);
         dl[t] += pg.ds[t] * sgs[t] + pg.dmu[t] * O[t];
         dxa[t] += pg.dmu[t];
         add_if(out.offsets ? out.offsets + (a * kNOff + j) * 3 + t : nullptr, pg.dmu[t] * l[t]);
         bad |= !isfinite(pg.dmu[t]) || !isfinite(pg.ds[t]);
       }
-      for (int t = 0; t < 4; ++t) dZ[idx[7 + t]] = dq[t];
+#pragma unroll
+      for (int t = 0; t < 4; ++t) dz[7 + t] = dq[t];
+#pragma unroll
+      for (int t = 0; t < 11; ++t) {
+        sc_dZ[sc_at(r, idx[t], kOut)] = dz[t];
+        w2_axpy(m, idx[t], dz[t], dH);
+      }
     }
-    // hidden layer: dH_pre = (W2^T dZ) * [H > 0]; input: dX = W1^T dH_pre
-    float dH[kHidden];
+    // hidden layer: dH_pre = (W2^T dZ) * [H > 0]
+#pragma unroll
     for (int h = 0; h < kHidden; ++h) {
-      float acc = 0.f;
-      if (H[h] > 0.f)
-        for (int t = 0; t < kOut; ++t) acc = fmaf(m.W2[t][h], dZ[t], acc);
-      dH[h] = acc;
+      dH[h] = H[h] > 0.f ? dH[h] : 0.f;
+      sc_dH[sc_at(r, h, kHidden)] = dH[h];
     }
     if (any) {
+      // input: dX = W1^T dH_pre (feature part to out.feat, direction part to the anchor position)
       float dX[kMaxIn];
-      for (int j = 0; j < in_dim; ++j) {
-        float acc = 0.f;
-        for (int h = 0; h < kHidden; ++h) acc = fmaf(m.W1[h][j], dH[h], acc);
-        dX[j] = acc;
+#pragma unroll
+      for (int j = 0; j < kMaxIn; ++j) dX[j] = 0.f;
+#pragma unroll
+      for (int i = 0; i < kHidden; ++i) {
+        const float4* w = reinterpret_cast<const float4*>(m.W1[i]);
+#pragma unroll
+        for (int qd = 0; qd < kMaxIn / 4; ++qd) {
+          const float4 ww = w[qd];
+          dX[4 * qd] = fmaf(ww.x, dH[i], dX[4 * qd]); dX[4 * qd + 1] = fmaf(ww.y, dH[i], dX[4 * qd + 1]);
+          dX[4 * qd + 2] = fmaf(ww.z, dH[i], dX[4 * qd + 2]); dX[4 * qd + 3] = fmaf(ww.w, dH[i], dX[4 * qd + 3]);
+        }
       }
+#pragma unroll
       for (int j = 0; j < kFeat; ++j) add_if(out.feat ? out.feat + a * kFeat + j : nullptr, dX[j]);
       // unit view direction dir = (x - o)/|x - o|: d dir / dx = (I - dir dir^T) / |x - o|
-      const float dr0 = X[32], dr1 = X[33], dr2 = X[34];
-      const float dd = dr0 * dX[32] + dr1 * dX[33] + dr2 * dX[34];
-      dxa[0] += (dX[32] - dr0 * dd) * idist;
-      dxa[1] += (dX[33] - dr1 * dd) * idist;
-      dxa[2] += (dX[34] - dr2 * dd) * idist;
-      if (in_dim == 36) { dxa[0] += dX[35] * dr0; dxa[1] += dX[35] * dr1; dxa[2] += dX[35] * dr2; }
+      const float dd = dir0 * dX[32] + dir1 * dX[33] + dir2 * dX[34];
+      dxa[0] += (dX[32] - dir0 * dd) * idist;
+      dxa[1] += (dX[33] - dir1 * dd) * idist;
+      dxa[2] += (dX[34] - dir2 * dd) * idist;
+      if (in_dim == 36) { dxa[0] += dX[35] * dir0; dxa[1] += dX[35] * dir1; dxa[2] += dX[35] * dir2; }
+#pragma unroll
       for (int t = 0; t < 3; ++t) {
         add_if(out.x ? out.x + 3 * a + t : nullptr, dxa[t]);
         add_if(out.log_l ? out.log_l + 3 * a + t : nullptr, dl[t] * l[t]);
       }
     }
     if (bad) set_flag(err, kFlagNonfinite);
-    // row scratch for the weight gradients, in 32-row blocks (sc_at)
-    for (int t = 0; t < kOut; ++t) sc_dZ[sc_at(r, t, kOut)] = dZ[t];
-    for (int h = 0; h < kHidden; ++h) { sc_H[sc_at(r, h, kHidden)] = H[h]; sc_dH[sc_at(r, h, kHidden)] = dH[h]; }
-    for (int j = 0; j < in_dim; ++j) sc_X[sc_at(r, j, kMaxIn)] = X[j];
   }
 }
 
