@@ -270,6 +270,35 @@ typedef struct pgs_tune_entry {
 pgs_status pgs_autotune(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
                         const pgs_image_grad_ptrs* grad, const pgs_param_grad_ptrs* pg, int reps,
                         pgs_tune_entry* entries, int max_entries, int* n_entries, cudaStream_t stream);
+/* Enhanced depth prior (Step 2 of the batch-level progressive training,
+ * Sec. 3.4; the threshold tau_d = 1 is given in the supplementary
+ * implementation details).  For the batch `cams`:
+ *  1. per view, the scale and shift of the pseudo depth D_p that fit the
+ *     sparse points' view depths by least squares (points sampled bilinearly
+ *     in D_p where they project): D~_p = s D_p + t;
+ *  2. per pixel, the re-projection error E: the pixel's 3D point at depth D~_p
+ *     is projected into each of the view's k nearest batch views (by camera
+ *     centre), lifted there with that view's D~_p (bilinear), projected back;
+ *     E = the smallest pixel distance over the neighbours where the round trip
+ *     is defined;
+ *  3. D~_f = D~_p where E <= tau_d or no neighbour could check the pixel, else
+ *     0 (also 0 where D_p <= 0); mask = 1 where D~_f is kept.
+ * d_pseudo: per-pixel pseudo depth in the image arena layout (<= 0 = none);
+ * d_points: float[n_points][3] world points (the sparse cloud); outputs, all
+ * device and caller-owned: d_prior_out and d_mask_out [pixels] (the loss's
+ * depth prior and mask), d_scale_shift float[n_views][2] ((1, 0) for a view
+ * with fewer than two usable points), d_err_out [pixels] optional (E, or -1
+ * where unchecked).  k_neighbors in 1..4 (clamped to n_views - 1), tau_d > 0
+ * in pixels.  Uses the scene's render parameters (near plane) and workspace. */
+typedef struct pgs_prior_params {
+  float tau_d;
+  int32_t k_neighbors;
+} pgs_prior_params;
+pgs_status pgs_filter_depth_prior(pgs_scene* s, const pgs_camera* cams, int n_views, const float* d_pseudo,
+                                  const float* d_points, int64_t n_points, const pgs_prior_params* pp,
+                                  float* d_prior_out, float* d_mask_out, float* d_scale_shift, float* d_err_out,
+                                  cudaStream_t stream);
+
 /* The scene's current render parameters (as created, or as the autotuner set them). */
 pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out);
 

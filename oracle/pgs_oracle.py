@@ -574,3 +574,145 @@ def tile_ranges(sorted_tiles: np.ndarray, n_tiles: int) -> np.ndarray:
     if prev is not None:
         r[prev, 1] = len(sorted_tiles)
     return r
+
+
+# ------------------------------------------------------------------ enhanced depth prior (Sec. 3.4, Step 2)
+# Reading of the paper's description (it gives the steps, not the formulas):
+# the pseudo depth D_p of view v is brought to the sparse points' scale by the
+# least-squares scale and shift (s_v, t_v) of z_k ~ s D_p(u_k) + t over the
+# points k that project into v (D_p sampled bilinearly at u_k, pixel centres at
+# +1/2); the re-projection error E(p) of pixel p of view a is the pixel
+# distance after the round trip a -> b -> a through the rescaled pseudo depths
+# of a and of b (b read bilinearly), minimised over the k batch views nearest
+# to a by camera centre; the filtered prior keeps D~_p(p) where E(p) <= tau_d
+# (1 in the supplementary) or where no neighbour could check p, and is 0
+# elsewhere or where D_p(p) <= 0.
+# E is a difference of pixel positions of order 10^3 carried through ~20 FP32
+# operations: its FP32 reach is about 10 ulp of 10^3, i.e. a few 1e-3 px.
+AMB_PRIOR_E = 2e-2      # px: decisions with E this close to tau_d are flagged
+AMB_PRIOR_EDGE = 1e-3   # px: a bilinear footprint this close to the frame edge may be in or out in FP32
+# On a steep footprint (the four samples differ by more than PRIOR_STEEP of the
+# value, e.g. across the edge of a wrong region of the pseudo depth) the read
+# depth moves by (jump / 1 px) per pixel of position error, so FP32 rounding of
+# the projected position can move E by a tenth of a pixel: the reach there is
+# AMB_PRIOR_E_STEEP.
+PRIOR_STEEP = 0.02
+AMB_PRIOR_E_STEEP = 0.25
+
+
+def _prior_bilinear(dp: torch.Tensor, x: torch.Tensor, y: torch.Tensor):
+    """Bilinear read of dp [H, W] at pixel coordinates (centres at +1/2).
+    Returns (value, defined, near_edge, steep)."""
+    H, W = dp.shape
+    u, w = x - 0.5, y - 0.5
+    fu, fw = torch.floor(u), torch.floor(w)
+    inside = (fu >= 0) & (fw >= 0) & (fu + 1 <= W - 1) & (fw + 1 <= H - 1)
+    near = ((u.abs() < AMB_PRIOR_EDGE) | (w.abs() < AMB_PRIOR_EDGE) | ((u - (W - 1)).abs() < AMB_PRIOR_EDGE)
+            | ((w - (H - 1)).abs() < AMB_PRIOR_EDGE))
+    i0 = fu.clamp(0, W - 2).long()
+    j0 = fw.clamp(0, H - 2).long()
+    a, b = dp[j0, i0], dp[j0, i0 + 1]
+    c, d = dp[j0 + 1, i0], dp[j0 + 1, i0 + 1]
+    au, aw = u - fu, w - fw
+    val = (1 - aw) * ((1 - au) * a + au * b) + aw * ((1 - au) * c + au * d)
+    ok = inside & (a > 0) & (b > 0) & (c > 0) & (d > 0)
+    hi = torch.maximum(torch.maximum(a, b), torch.maximum(c, d))
+    lo = torch.minimum(torch.minimum(a, b), torch.minimum(c, d))
+    steep = (hi - lo) > PRIOR_STEEP * val.abs()
+    return val, ok, near, steep
+
+
+def _to_cam(cam: dict, x: torch.Tensor) -> torch.Tensor:
+    return x @ cam["R"].T + cam["t"]
+
+
+def _to_world(cam: dict, c: torch.Tensor) -> torch.Tensor:
+    return (c - cam["t"]) @ cam["R"]
+
+
+def prior_scale_shift(cam: dict, dp: torch.Tensor, points: torch.Tensor, near: float):
+    """Least-squares (s, t) of the points' view depths against the bilinear pseudo depth
+    (a library least-squares solve on [D_p, 1]); (1, 0) with fewer than two points."""
+    c = _to_cam(cam, points)
+    front = c[:, 2] > near
+    zc = torch.where(front, c[:, 2], torch.ones_like(c[:, 2]))
+    px = cam["fx"] * c[:, 0] / zc + cam["cx"]
+    py = cam["fy"] * c[:, 1] / zc + cam["cy"]
+    d, ok, _, _ = _prior_bilinear(dp, px, py)
+    use = front & ok
+    if int(use.sum()) < 2:
+        return 1.0, 0.0, int(use.sum())
+    A = torch.stack([d[use], torch.ones_like(d[use])], 1)
+    sol = torch.linalg.lstsq(A, c[use, 2:3]).solution
+    s, t = float(sol[0, 0]), float(sol[1, 0])
+    if not math.isfinite(s) or float(d[use].var(unbiased=False)) <= 0.0:
+        return 1.0, 0.0, int(use.sum())
+    return s, t, int(use.sum())
+
+
+def nearest_views(cams: Sequence[dict], k: int) -> List[List[int]]:
+    """The k other views nearest by camera centre (ties by index)."""
+    out = []
+    for a, ca in enumerate(cams):
+        d = sorted((float(((ca["center"] - cb["center"]) ** 2).sum()), b) for b, cb in enumerate(cams) if b != a)
+        out.append([b for _, b in d[:min(k, len(cams) - 1)]])
+    return out
+
+
+def filter_depth_prior(cams_in: Sequence, pseudo: Sequence[torch.Tensor], points, tau_d: float = 1.0, k: int = 2,
+                       near: float = 0.01) -> dict:
+    """Enhanced depth prior of a batch (see the reading above).  pseudo[v]: [H, W]
+    pseudo depth (<= 0 = none); points: [n, 3] world.  Returns per view the
+    filtered prior, mask, error E (-1 = unchecked), ambiguity flags, the
+    steep-footprint map (E ill-conditioned there), and (s, t)."""
+    cams = [camera(c) for c in cams_in]
+    pts = _t(points).reshape(-1, 3)
+    dps = [_t(p) for p in pseudo]
+    st = [prior_scale_shift(c, dp, pts, near) for c, dp in zip(cams, dps)]
+    nbr = nearest_views(cams, k)
+    views = []
+    for a, ca in enumerate(cams):
+        H, W = ca["H"], ca["W"]
+        s, t, _ = st[a]
+        dp = dps[a]
+        d = s * dp + t
+        have = (dp > 0) & (d > 0)
+        vv, uu = torch.meshgrid(torch.arange(H, dtype=DT) + 0.5, torch.arange(W, dtype=DT) + 0.5, indexing="ij")
+        pc = torch.stack([d * (uu - ca["cx"]) / ca["fx"], d * (vv - ca["cy"]) / ca["fy"], d], -1)
+        xw = _to_world(ca, pc.reshape(-1, 3))
+        best = torch.full((H * W,), float("inf"), dtype=DT)
+        checked = torch.zeros(H * W, dtype=torch.bool)
+        amb = torch.zeros(H * W, dtype=torch.bool)
+        steep = torch.zeros(H * W, dtype=torch.bool)
+        for b in nbr[a]:
+            cb = cams[b]
+            sb, tb, _ = st[b]
+            c1 = _to_cam(cb, xw)
+            front1 = c1[:, 2] > near
+            z1 = torch.where(front1, c1[:, 2], torch.ones_like(c1[:, 2]))
+            qx = cb["fx"] * c1[:, 0] / z1 + cb["cx"]
+            qy = cb["fy"] * c1[:, 1] / z1 + cb["cy"]
+            rb, okb, nearb, steepb = _prior_bilinear(dps[b], qx, qy)
+            db = sb * rb + tb
+            pb = torch.stack([db * (qx - cb["cx"]) / cb["fx"], db * (qy - cb["cy"]) / cb["fy"], db], -1)
+            c2 = _to_cam(ca, _to_world(cb, pb))
+            front2 = c2[:, 2] > near
+            z2 = torch.where(front2, c2[:, 2], torch.ones_like(c2[:, 2]))
+            rx = ca["fx"] * c2[:, 0] / z2 + ca["cx"] - uu.reshape(-1)
+            ry = ca["fy"] * c2[:, 1] / z2 + ca["cy"] - vv.reshape(-1)
+            e = torch.sqrt(rx * rx + ry * ry)
+            valid = front1 & okb & (db > 0) & front2
+            best = torch.where(valid, torch.minimum(best, e), best)
+            checked |= valid
+            steep |= valid & steepb
+            amb |= front1 & nearb
+        have_f = have.reshape(-1)
+        keep = have_f & (~checked | (best <= tau_d))
+        amb |= have_f & checked & ((best - tau_d).abs() <= AMB_PRIOR_E)
+        amb |= have_f & checked & steep & ((best - tau_d).abs() <= AMB_PRIOR_E_STEEP)
+        E = torch.where(checked & have_f, best, torch.full_like(best, -1.0))
+        views.append(dict(prior=torch.where(keep, d.reshape(-1), torch.zeros_like(best)).reshape(H, W),
+                          mask=keep.to(DT).reshape(H, W), err=E.reshape(H, W), amb=amb.reshape(H, W),
+                          steep=steep.reshape(H, W),
+                          scale=s, shift=t, n_points=st[a][2]))
+    return dict(views=views, neighbours=nbr)

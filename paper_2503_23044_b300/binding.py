@@ -103,6 +103,10 @@ class Stats(C.Structure):
                 ("tiles", C.c_int64), ("pixels", C.c_int64), ("flags", C.c_uint32)]
 
 
+class PriorParams(C.Structure):
+    _fields_ = [("tau_d", C.c_float), ("k_neighbors", C.c_int32)]
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("blend_batch", C.c_int32), ("ms", C.c_float)]
 
@@ -112,7 +116,7 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
-                "pgs_scene_get_params")
+                "pgs_scene_get_params", "pgs_filter_depth_prior")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad")
 
 
@@ -151,6 +155,7 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_autotune.argtypes = [vp, P(Camera), i32, P(ImagePtrs), P(ImageGradPtrs), P(ParamGradPtrs), i32,
                                P(TuneEntry), i32, P(i32), vp]
     L.pgs_scene_get_params.argtypes = [vp, P(RenderParams)]
+    L.pgs_filter_depth_prior.argtypes = [vp, P(Camera), i32, vp, vp, i64, P(PriorParams), vp, vp, vp, vp, vp]
 
 
 def check(status: int) -> None:
@@ -355,6 +360,22 @@ class Scene:
         check(lib().pgs_autotune(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(grads.ptrs()),
                                  C.byref(pg), reps, out, 16, C.byref(n), _stream(stream)))
         return [dict(tile_w=e.tile_w, tile_h=e.tile_h, blend_batch=e.blend_batch, ms=e.ms) for e in out[:n.value]]
+
+    def filter_depth_prior(self, cams, pseudo: torch.Tensor, points: torch.Tensor, tau_d: float = 1.0,
+                           k_neighbors: int = 2, with_error: bool = False, stream=None, packed=None) -> dict:
+        """Enhanced depth prior (pgs_filter_depth_prior): pseudo depth in the arena layout and world
+        points [n, 3] -> dict(prior, mask, scale_shift [views, 2], err)."""
+        n = pseudo.numel()
+        out = dict(prior=torch.empty(n, device=pseudo.device), mask=torch.empty(n, device=pseudo.device),
+                   scale_shift=torch.empty(len(cams), 2, device=pseudo.device),
+                   err=torch.empty(n, device=pseudo.device) if with_error else None)
+        cc = packed if packed is not None else pack_cameras(cams)
+        pts = points.contiguous()
+        pp = PriorParams(tau_d, k_neighbors)
+        check(lib().pgs_filter_depth_prior(self.handle, cc, len(cams), _ptr(pseudo), _ptr(pts) if pts.numel() else None,
+                                           pts.shape[0], C.byref(pp), _ptr(out["prior"]), _ptr(out["mask"]),
+                                           _ptr(out["scale_shift"]), _ptr(out["err"]), _stream(stream)))
+        return out
 
     def params(self) -> dict:
         p = RenderParams()

@@ -92,6 +92,7 @@ struct pgs_scene {
   uint2* ranges = nullptr;
   uint32_t *order_k = nullptr, *order_v = nullptr, *order_kb = nullptr, *order_vb = nullptr;  // tile queue
   uint32_t* queue_ctr = nullptr;         // [0] forward, [1] backward
+  float *prior_partials = nullptr, *prior_means = nullptr;   // enhanced depth prior fit
   uint32_t *cull_flags = nullptr, *cull_offs = nullptr, *rows = nullptr;
   float *sc_dZ = nullptr, *sc_H = nullptr, *sc_dH = nullptr, *sc_X = nullptr, *wg_partials = nullptr;
   int wg_blocks = 0;
@@ -165,7 +166,7 @@ void pgs_scene_destroy(pgs_scene* s) {
                 s->ptile_b, s->pg_a, s->pg_b, s->ranges, s->cull_flags, s->cull_offs, s->rows, s->sc_dZ, s->sc_H,
                 s->sc_dH, s->sc_X, s->wg_partials, s->d_cnt, s->d_tot, s->scan_sums, s->sort_mem, s->d_flags,
                 s->loss_counts, s->loss_partials, s->order_k, s->order_v, s->order_kb, s->order_vb,
-                s->queue_ctr};
+                s->queue_ctr, s->prior_partials, s->prior_means};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : s->ev)
@@ -233,6 +234,8 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   ALLOC(s->order_kb, s->max_tiles);
   ALLOC(s->order_vb, s->max_tiles);
   ALLOC(s->queue_ctr, 2);
+  ALLOC(s->prior_partials, (long long)kMaxViews * kPriorBlocks * 3);
+  ALLOC(s->prior_means, (long long)kMaxViews * 4);
   ALLOC(s->d_cnt, 8);
   ALLOC(s->d_tot, 4);
   ALLOC(s->scan_sums, kScanBlocks);
@@ -535,6 +538,45 @@ pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n) {
     PGS_CUDA(cudaEventSynchronize(s->ev[k][1]));
     PGS_CUDA(cudaEventElapsedTime(&ms[k], s->ev[k][0], s->ev[k][1]));
   }
+  return PGS_OK;
+}
+
+pgs_status pgs_filter_depth_prior(pgs_scene* s, const pgs_camera* cams, int n_views, const float* d_pseudo,
+                                  const float* d_points, int64_t n_points, const pgs_prior_params* pp,
+                                  float* d_prior_out, float* d_mask_out, float* d_scale_shift, float* d_err_out,
+                                  cudaStream_t st) {
+  if (!s || !pp || !d_pseudo || !d_prior_out || !d_mask_out || !d_scale_shift)
+    return fail(PGS_ERR_INVALID_ARG, "null argument");
+  if (n_points < 0 || (n_points > 0 && !d_points)) return fail(PGS_ERR_INVALID_ARG, "points");
+  if (!(pp->tau_d > 0.f) || pp->k_neighbors < 1 || pp->k_neighbors > kPriorMaxK)
+    return fail(PGS_ERR_INVALID_ARG, "tau_d %g, k_neighbors %d (1..%d)", pp->tau_d, pp->k_neighbors, kPriorMaxK);
+  BatchDev b;
+  pgs_status r = build_batch(s, cams, n_views, b);
+  if (r) return r;
+  // the k nearest other views by camera centre (ties by index)
+  PriorArgs pa;
+  pa.k = std::min(pp->k_neighbors, n_views - 1);
+  pa.tau_d = pp->tau_d;
+  for (int a = 0; a < kMaxViews; ++a)
+    for (int i = 0; i < kPriorMaxK; ++i) pa.nbr[a][i] = -1;
+  for (int a = 0; a < n_views; ++a) {
+    std::vector<std::pair<double, int>> d;
+    for (int c = 0; c < n_views; ++c) {
+      if (c == a) continue;
+      double q = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        const double e = (double)b.v[a].center[k] - (double)b.v[c].center[k];
+        q += e * e;
+      }
+      d.emplace_back(q, c);
+    }
+    std::sort(d.begin(), d.end());
+    for (int i = 0; i < pa.k; ++i) pa.nbr[a][i] = d[i].second;
+  }
+  launch_prior_filter(b, pa, d_pseudo, d_points, (long long)n_points, s->prior_partials, s->prior_means,
+                      d_scale_shift, d_prior_out, d_mask_out, d_err_out, s->num_sms, st);
+  s->launches += kPriorLaunches;
+  PGS_CUDA(cudaGetLastError());
   return PGS_OK;
 }
 

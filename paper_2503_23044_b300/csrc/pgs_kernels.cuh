@@ -8,6 +8,14 @@ constexpr int kScanBlocks = 592;   // 4 x 148 SMs
 constexpr int kLossBlocks = 1184;  // 8 x 148 SMs
 // kernels enqueued by the multi-kernel launch helpers
 constexpr int kScanLaunches = 3, kLossLaunches = 3, kWgradLaunches = 2;
+constexpr int kPriorBlocks = 64, kPriorLaunches = 5, kPriorMaxK = 4;
+
+// enhanced depth prior: the k nearest batch views of each view (-1 = none) and the filter threshold
+struct PriorArgs {
+  int nbr[kMaxViews][kPriorMaxK];
+  int k;
+  float tau_d;
+};
 
 struct DecodeOut {
   float *mu, *opacity, *color, *scale, *quat;
@@ -83,6 +91,11 @@ __host__ __device__ __forceinline__ size_t sc_at(long long r, int f, int width) 
   return ((size_t)(r / kScBlock) * width + f) * kScBlock + (size_t)(r % kScBlock);
 }
 __host__ __device__ __forceinline__ long long sc_rows(long long cap) { return (cap + kScBlock - 1) / kScBlock * kScBlock; }
+
+// k_prior.cu
+void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp, const float* pts, long long n_pts,
+                         float* partials, float* means, float* scale_shift, float* prior_out, float* mask_out,
+                         float* err_out, int num_sms, cudaStream_t st);
 
 // k_backward.cu
 __global__ void k_project_bwd_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N,

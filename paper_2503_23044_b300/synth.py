@@ -263,7 +263,7 @@ def anchor_scene(spec: SceneSpec | str, n_anchors: Optional[int] = None, seed: O
     return dict(kind="anchor", x=_f32(x), level=np.ascontiguousarray(level.astype(np.int32)),
                 log_l=_f32(log_l), offsets=_f32(offsets), feat=_f32(feat), mlp=mlp, cameras=cams,
                 n_levels=len(spec.voxel_sizes), lod_d0=float(spec.lod_d0), terrain=terrain,
-                name=spec.name)
+                extent=float(spec.extent), name=spec.name)
 
 
 def tiny_anchor_scene(n_anchors: int = 4, seed: int = 0, width: int = 24, height: int = 20,
@@ -403,3 +403,46 @@ def random_maps(cams: Sequence[Camera], seed: int) -> List[dict]:
         n[2] = -1.0 + n[2] * 0.1
         out.append(dict(rgb=rgb, depth=depth, normal=n))
     return out
+
+
+# ---------------------------------------------------------------- depth-prior inputs (Sec. 3.4, Step 2)
+def sparse_points(terrain: Terrain, extent: float, n: int, seed: int = 0, noise: float = 0.0) -> np.ndarray:
+    """Stand-in for the sparse SfM cloud: n points on the heightfield over the
+    scene extent (optionally jittered by N(0, noise) per axis), float32 [n, 3]."""
+    rng = np.random.default_rng(seed)
+    xy = rng.uniform(-extent / 2.0, extent / 2.0, (n, 2))
+    z = terrain.height(xy[:, 0], xy[:, 1])
+    p = np.concatenate([xy, z[:, None]], 1)
+    if noise > 0:
+        p = p + rng.normal(0.0, noise, p.shape)
+    return _f32(p)
+
+
+def pseudo_depth(true_depth, valid, seed: int = 0, noise: float = 5e-4, n_blobs: int = 3,
+                 blob_radius=(0.05, 0.12), blob_factor=(1.3, 1.8)):
+    """Stand-in for a monocular depth estimate of one view: the true z-depth with
+    relative noise N(0, noise), wrong by a factor U[blob_factor] inside n_blobs
+    discs (radius a fraction of the image width), then expressed in an unknown
+    affine frame, D_p = (z - t) / s with s ~ U[0.5, 2], t ~ U[-0.5, 0.5]; 0 where
+    there is no depth.  Returns (D_p [H, W] float32 tensor, s, t, blob mask)."""
+    import torch
+    gen = torch.Generator().manual_seed(seed)
+    z = torch.as_tensor(true_depth, dtype=torch.float64).cpu()
+    ok = torch.as_tensor(valid).cpu().bool()
+    H, W = z.shape
+    z = z * (1.0 + noise * torch.randn(H, W, generator=gen, dtype=torch.float64))
+    blob = torch.zeros(H, W, dtype=torch.bool)
+    vv, uu = torch.meshgrid(torch.arange(H, dtype=torch.float64), torch.arange(W, dtype=torch.float64), indexing="ij")
+    for _ in range(n_blobs):
+        cx = float(torch.rand(1, generator=gen)) * W
+        cy = float(torch.rand(1, generator=gen)) * H
+        r = (blob_radius[0] + (blob_radius[1] - blob_radius[0]) * float(torch.rand(1, generator=gen))) * W
+        f = blob_factor[0] + (blob_factor[1] - blob_factor[0]) * float(torch.rand(1, generator=gen))
+        disc = (uu - cx) ** 2 + (vv - cy) ** 2 <= r * r
+        z = torch.where(disc, z * f, z)
+        blob |= disc
+    s = 0.5 + 1.5 * float(torch.rand(1, generator=gen))
+    t = -0.5 + float(torch.rand(1, generator=gen))
+    dp = torch.where(ok, (z - t) / s, torch.zeros_like(z))
+    dp = torch.where(ok & (dp > 0), dp, torch.zeros_like(dp))
+    return dp.float(), s, t, blob & ok
