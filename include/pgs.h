@@ -243,7 +243,8 @@ enum pgs_stage {
   PGS_STAGE_BLEND_BWD = 6,
   PGS_STAGE_PROJECT_BWD = 7,  /* projection (+ decoder input/activation) backward */
   PGS_STAGE_WGRAD = 8,        /* decoder weight-gradient reduction */
-  PGS_N_STAGES = 9
+  PGS_STAGE_PRIOR = 9,        /* enhanced depth prior (pgs_filter_depth_prior) */
+  PGS_N_STAGES = 10
 };
 pgs_status pgs_set_profiling(pgs_scene* s, int enable);
 pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);

@@ -716,3 +716,180 @@ def filter_depth_prior(cams_in: Sequence, pseudo: Sequence[torch.Tensor], points
                           steep=steep.reshape(H, W),
                           scale=s, shift=t, n_points=st[a][2]))
     return dict(views=views, neighbours=nbr)
+
+
+# ------------------------------------------------------------------ batch geometric NCC (Sec. 3.4, Step 3, Eq. 10)
+# Reading of Eq. 10 and the text around it:
+# * the rendered batch is split into pairs (views 2i-1, 2i counted from 1); in
+#   0-based indices pair i has the reference view 2i+1, whose patches are
+#   compared, and the partner view 2i, sampled through the homography;
+# * every pair draws N patch centres p (the random draw is an input here); a
+#   7 x 7 patch of reference pixels around p is mapped into the partner by the
+#   homography of the plane through the back-projected centre, with the
+#   rendered unbiased depth D_hat(p) and normal N_hat(p) of the reference view:
+#   plane m . X = 1 with m = N_hat / (D_hat (N_hat . r_p)), r_p = K_r^-1 p~,
+#   H = K_s (R + t m^T) K_r^-1 where X_s = R X_r + t maps reference to partner
+#   camera coordinates;
+# * NCC (zero-normalised cross-correlation) of the BT.601 luma of the two
+#   patches: the reference's at its 49 pixels, the partner's read bilinearly
+#   (pixel centres at +1/2) at the 49 warped positions,
+#   NCC = S_ab / sqrt((S_aa + eps)(S_bb + eps)) over centred sums, eps = 1e-6;
+# * a patch counts only if it lies inside the reference frame, the plane is
+#   defined (D_hat(p) > 0, |N_hat(p) . r_p| >= 1e-8), and every warped sample
+#   has the plane in front of both cameras and its whole bilinear footprint
+#   inside the partner frame;
+# * L_ncc = (1 / (B/2)) sum_i mean over pair i's valid patches of (1 - NCC),
+#   a pair without valid patches adding 0;
+# * sg[.]: with geo=True the partner image is a constant while the sampling
+#   positions keep their dependence on D_hat(p) and N_hat(p) (so Step 3 reaches
+#   the geometry); with geo=False the whole sampled partner patch is constant
+#   (gradients reach the reference colours only, the formula taken literally).
+NCC_HALF = 3
+NCC_EPS = 1e-6
+LUMA = (0.299, 0.587, 0.114)
+# an FP32 evaluation reaches the warped positions to ~1e-4 px (positions of
+# order 10^3 through a 3 x 3 product and a division): a sample this close to
+# the edge of the bilinear area may be in or out, and a sample this close to a
+# cell boundary may take the other cell's bilinear slope (the geometric
+# gradient jumps there; the sampled value does not)
+AMB_NCC_EDGE = 1e-3
+AMB_NCC_CELL = 1e-3
+AMB_NCC_FRONT = 1e-6    # relative: m . r_q or h_z this close to 0
+
+
+def ncc_pairs(n_views: int) -> List[tuple]:
+    """(reference, partner) view indices of the pairs of Eq. 10."""
+    return [(2 * i + 1, 2 * i) for i in range(n_views // 2)]
+
+
+def luma(rgb: torch.Tensor) -> torch.Tensor:
+    """BT.601 luma of a [3, ...] colour array."""
+    return LUMA[0] * rgb[0] + LUMA[1] * rgb[1] + LUMA[2] * rgb[2]
+
+
+def _kmat(cam: dict) -> torch.Tensor:
+    return torch.tensor([[cam["fx"], 0.0, cam["cx"]], [0.0, cam["fy"], cam["cy"]], [0.0, 0.0, 1.0]], dtype=DT)
+
+
+def plane_homography(cr: dict, cs: dict, m: torch.Tensor) -> torch.Tensor:
+    """Homographies [n, 3, 3] from reference pixels to partner pixels induced by
+    the planes m . X = 1 (m [n, 3], reference camera frame)."""
+    R = cs["R"] @ cr["R"].T
+    t = cs["t"] - R @ cr["t"]
+    A = R.unsqueeze(0) + t.view(1, 3, 1) * m.view(-1, 1, 3)
+    return _kmat(cs) @ A @ torch.linalg.inv(_kmat(cr))
+
+
+def _bilinear_area(x: torch.Tensor, y: torch.Tensor, W: int, H: int):
+    """(inside, near_edge, near_cell) of bilinear reads at pixel coordinates."""
+    u, w = x - 0.5, y - 0.5
+    inside = (torch.floor(u) >= 0) & (torch.floor(w) >= 0) & (torch.floor(u) + 1 <= W - 1) & \
+             (torch.floor(w) + 1 <= H - 1)
+    near = ((u.abs() < AMB_NCC_EDGE) | (w.abs() < AMB_NCC_EDGE) | ((u - (W - 1)).abs() < AMB_NCC_EDGE)
+            | ((w - (H - 1)).abs() < AMB_NCC_EDGE))
+    fu, fw = u - torch.floor(u), w - torch.floor(w)
+    cell = (fu < AMB_NCC_CELL) | (fu > 1 - AMB_NCC_CELL) | (fw < AMB_NCC_CELL) | (fw > 1 - AMB_NCC_CELL)
+    return inside, near, cell
+
+
+def _bilinear(img: torch.Tensor, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """Bilinear read of img [H, W] at pixel coordinates (centres at +1/2); the
+    caller guarantees the footprint is inside (indices are clamped only so that
+    invalid samples stay addressable)."""
+    H, W = img.shape
+    u, w = x - 0.5, y - 0.5
+    fu, fw = torch.floor(u), torch.floor(w)
+    i0 = fu.clamp(0, W - 2).long()
+    j0 = fw.clamp(0, H - 2).long()
+    au, aw = u - fu, w - fw
+    a, b = img[j0, i0], img[j0, i0 + 1]
+    c, d = img[j0 + 1, i0], img[j0 + 1, i0 + 1]
+    return (1 - aw) * ((1 - au) * a + au * b) + aw * ((1 - au) * c + au * d)
+
+
+def ncc(a: torch.Tensor, b: torch.Tensor, eps: float = NCC_EPS) -> torch.Tensor:
+    """Zero-normalised cross-correlation along the last axis, eps added to each
+    centred sum of squares."""
+    da = a - a.mean(-1, keepdim=True)
+    db = b - b.mean(-1, keepdim=True)
+    return (da * db).sum(-1) / torch.sqrt(((da * da).sum(-1) + eps) * ((db * db).sum(-1) + eps))
+
+
+def ncc_patches(cr: dict, cs: dict, ref: dict, part_rgb: torch.Tensor, centers: torch.Tensor, geo: bool = True,
+                eps: float = NCC_EPS) -> dict:
+    """Eq. 10 for one pair: NCC of the 7 x 7 reference patches at `centers`
+    (local pixel indices y W + x) against the partner read through the plane
+    homography.  ref: dict(rgb [3,H,W], depth [H,W] = D_hat, normal [3,H,W] =
+    N_hat) of the reference view (tensors may require grad); part_rgb [3,H,W]
+    the partner's colour.  Returns dict(ncc [n], valid [n], amb [n], cell [n],
+    warped [n, 49, 2])."""
+    W, H = cr["W"], cr["H"]
+    centers = torch.as_tensor(centers, dtype=torch.long).reshape(-1)
+    n = centers.numel()
+    cy, cx = centers // W, centers % W
+    inframe = (cx >= NCC_HALF) & (cx <= W - 1 - NCC_HALF) & (cy >= NCC_HALF) & (cy <= H - 1 - NCC_HALF)
+    cxc = cx.clamp(NCC_HALF, W - 1 - NCC_HALF)
+    cyc = cy.clamp(NCC_HALF, H - 1 - NCC_HALF)
+    d = ref["depth"][cyc, cxc]
+    nr = ref["normal"][:, cyc, cxc].T                                    # [n, 3]
+    rp = torch.stack([(cxc.to(DT) + 0.5 - cr["cx"]) / cr["fx"], (cyc.to(DT) + 0.5 - cr["cy"]) / cr["fy"],
+                      torch.ones(n, dtype=DT)], 1)
+    c = (nr * rp).sum(1)
+    plane = inframe & (d > 0) & (c.abs() >= 1e-8)
+    den = torch.where(plane, d * c, torch.ones_like(c))
+    m = nr / den.unsqueeze(1)                                            # m . X = 1
+    Hm = plane_homography(cr, cs, m)                                     # [n, 3, 3]
+    off = torch.arange(-NCC_HALF, NCC_HALF + 1)
+    oy, ox = torch.meshgrid(off, off, indexing="ij")
+    qx = (cxc.view(-1, 1) + ox.reshape(1, -1))                            # [n, 49] reference pixels
+    qy = (cyc.view(-1, 1) + oy.reshape(1, -1))
+    q = torch.stack([qx.to(DT) + 0.5, qy.to(DT) + 0.5, torch.ones(n, qx.shape[1], dtype=DT)], -1)
+    h = torch.einsum("nij,nkj->nki", Hm, q)                              # [n, 49, 3]
+    rq = torch.stack([(q[..., 0] - cr["cx"]) / cr["fx"], (q[..., 1] - cr["cy"]) / cr["fy"], q[..., 2]], -1)
+    mr = (m.unsqueeze(1) * rq).sum(-1)
+    hz = torch.where(h[..., 2] > 0, h[..., 2], torch.ones_like(h[..., 2]))
+    ux, uy = h[..., 0] / hz, h[..., 1] / hz
+    Ws, Hs = cs["W"], cs["H"]
+    inside, near, cell = _bilinear_area(ux.detach(), uy.detach(), Ws, Hs)
+    front = (mr > 0) & (h[..., 2] > 0)
+    valid = plane & (front & inside).all(1)
+    a = luma(ref["rgb"][:, qy, qx])                                      # [n, 49]
+    g = luma(part_rgb).detach()
+    if geo:
+        b = _bilinear(g, ux, uy)
+    else:
+        b = _bilinear(g, ux.detach(), uy.detach()).detach()
+    val = ncc(a, b, eps)
+    scale_mr = mr.detach().abs().amax(1).clamp(min=1e-30)
+    amb = plane & (near | (mr.detach().abs() < AMB_NCC_FRONT * scale_mr.unsqueeze(1))
+                   | (h[..., 2].detach().abs() < AMB_NCC_FRONT * h[..., 2].detach().abs().amax(1, keepdim=True))).any(1)
+    return dict(ncc=val, valid=valid, amb=amb, cell=plane & cell.any(1), warped=torch.stack([ux, uy], -1))
+
+
+def ncc_loss(cams_in: Sequence, maps: Sequence[dict], centers, geo: bool = True, eps: float = NCC_EPS,
+             lam: float = 1.0, grad: bool = True) -> dict:
+    """L_ncc of Eq. 10 over the batch (reading above) and, with grad=True, its
+    gradients with respect to every view's rgb, depth (D_hat) and normal
+    (N_hat), scaled by lam (torch.autograd in FP64).  maps[v]: dict(rgb
+    [3,H,W], depth [H,W], normal [3,H,W]); centers: [B/2, N] local pixel
+    indices of the reference views."""
+    cams = [camera(c) for c in cams_in]
+    pairs = ncc_pairs(len(cams))
+    leaves = [{k: _t(mp[k]).clone().requires_grad_(grad) for k in ("rgb", "depth", "normal")} for mp in maps]
+    centers = torch.as_tensor(np.asarray(centers), dtype=torch.long).reshape(len(pairs), -1) if pairs else None
+    per = []
+    total = torch.zeros((), dtype=DT)
+    for i, (r, s) in enumerate(pairs):
+        out = ncc_patches(cams[r], cams[s], leaves[r], leaves[s]["rgb"], centers[i], geo, eps)
+        nv = int(out["valid"].sum())
+        li = ((1.0 - out["ncc"]) * out["valid"]).sum() / nv if nv > 0 else torch.zeros((), dtype=DT)
+        total = total + li
+        per.append(dict(ncc=out["ncc"].detach(), valid=out["valid"], amb=out["amb"], cell=out["cell"],
+                        n_valid=nv, loss=float(li)))
+    L = total / len(pairs) if pairs else total
+    res = dict(loss=float(L), pairs=per)
+    if grad and pairs:
+        (lam * L).backward()
+        res["grads"] = [{k: (lf[k].grad if lf[k].grad is not None else torch.zeros_like(lf[k])).detach()
+                         for k in ("rgb", "depth", "normal")} for lf in leaves]
+    return res

@@ -117,7 +117,8 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
                 "pgs_scene_get_params", "pgs_filter_depth_prior")
-STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad")
+STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad",
+          "prior")
 
 
 def _declare(L: C.CDLL) -> None:
@@ -362,13 +363,23 @@ class Scene:
         return [dict(tile_w=e.tile_w, tile_h=e.tile_h, blend_batch=e.blend_batch, ms=e.ms) for e in out[:n.value]]
 
     def filter_depth_prior(self, cams, pseudo: torch.Tensor, points: torch.Tensor, tau_d: float = 1.0,
-                           k_neighbors: int = 2, with_error: bool = False, stream=None, packed=None) -> dict:
+                           k_neighbors: int = 2, with_error: bool = False, stream=None, packed=None,
+                           out: Optional[dict] = None) -> dict:
         """Enhanced depth prior (pgs_filter_depth_prior): pseudo depth in the arena layout and world
-        points [n, 3] -> dict(prior, mask, scale_shift [views, 2], err)."""
+        points [n, 3] -> dict(prior, mask, scale_shift [views, 2], err).  `out` may supply the
+        prior / mask / scale_shift buffers (e.g. a Targets' prior and mask)."""
         n = pseudo.numel()
-        out = dict(prior=torch.empty(n, device=pseudo.device), mask=torch.empty(n, device=pseudo.device),
-                   scale_shift=torch.empty(len(cams), 2, device=pseudo.device),
-                   err=torch.empty(n, device=pseudo.device) if with_error else None)
+        given = out or {}
+        out = dict(prior=given.get("prior", None), mask=given.get("mask", None),
+                   scale_shift=given.get("scale_shift", None), err=None)
+        if out["prior"] is None:
+            out["prior"] = torch.empty(n, device=pseudo.device)
+        if out["mask"] is None:
+            out["mask"] = torch.empty(n, device=pseudo.device)
+        if out["scale_shift"] is None:
+            out["scale_shift"] = torch.empty(len(cams), 2, device=pseudo.device)
+        if with_error:
+            out["err"] = torch.empty(n, device=pseudo.device)
         cc = packed if packed is not None else pack_cameras(cams)
         pts = points.contiguous()
         pp = PriorParams(tau_d, k_neighbors)

@@ -573,9 +573,11 @@ pgs_status pgs_filter_depth_prior(pgs_scene* s, const pgs_camera* cams, int n_vi
     std::sort(d.begin(), d.end());
     for (int i = 0; i < pa.k; ++i) pa.nbr[a][i] = d[i].second;
   }
+  prof_mark(s, PGS_STAGE_PRIOR, 0, st);
   launch_prior_filter(b, pa, d_pseudo, d_points, (long long)n_points, s->prior_partials, s->prior_means,
                       d_scale_shift, d_prior_out, d_mask_out, d_err_out, s->num_sms, st);
   s->launches += kPriorLaunches;
+  prof_mark(s, PGS_STAGE_PRIOR, 1, st);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;
 }

@@ -127,6 +127,16 @@ class Terrain:
             h = h + xp.sin(float(self.omega[k, 0]) * x + float(self.omega[k, 1]) * y + float(self.phase[k]))
         return self.amplitude * h
 
+    def grad(self, x, y):
+        """(dh/dx, dh/dy) of the heightfield."""
+        xp = np if isinstance(x, np.ndarray) else _torch()
+        gx, gy = 0.0, 0.0
+        for k in range(self.omega.shape[0]):
+            c = xp.cos(float(self.omega[k, 0]) * x + float(self.omega[k, 1]) * y + float(self.phase[k]))
+            gx = gx + float(self.omega[k, 0]) * c
+            gy = gy + float(self.omega[k, 1]) * c
+        return self.amplitude * gx, self.amplitude * gy
+
 
 def _torch():
     import torch
@@ -303,7 +313,9 @@ def march_targets(terrain: Terrain, cam: Camera, stride: int = 4, t_max: float =
     """Analytic ray-march of the heightfield (independent of both renderers).
 
     Returns target RGB [3,H,W], true z-depth [H,W], depth prior
-    z * (1 + N(0, 0.02)) [H,W] and a {0,1} mask of rays that hit.  Rays are
+    z * (1 + N(0, 0.02)) [H,W], a {0,1} mask of rays that hit and the unit
+    surface normal in the camera frame, facing the camera [3,H,W] (0 where
+    the ray misses).  Rays are
     marched at every ``stride``-th pixel and the result is held over the
     stride x stride block (the target only shapes the loss workload).
     """
@@ -351,6 +363,11 @@ def march_targets(terrain: Terrain, cam: Camera, stride: int = 4, t_max: float =
     gen = torch.Generator(device="cpu").manual_seed(seed)
     noise = torch.randn(n, generator=gen, dtype=torch.float64).to(device)
     prior = depth * (1.0 + 0.02 * noise) * mask
+    gx, gy = terrain.grad(P[:, 0], P[:, 1])
+    nw = torch.stack([-gx, -gy, torch.ones_like(gx)], 1)
+    nc = (nw / nw.norm(dim=1, keepdim=True)) @ R.T          # camera frame
+    nc = torch.where(((nc * dcam.reshape(n, 3)).sum(1) > 0)[:, None], -nc, nc)
+    normal = nc.T * mask
 
     def up(a):
         a = a.reshape(-1, hs, ws)
@@ -358,7 +375,8 @@ def march_targets(terrain: Terrain, cam: Camera, stride: int = 4, t_max: float =
         return a[:, :H, :W]
 
     return dict(rgb=up(rgb).float().contiguous(), depth=up(depth * mask)[0].float().contiguous(),
-                prior=up(prior)[0].float().contiguous(), mask=up(mask.double())[0].float().contiguous())
+                prior=up(prior)[0].float().contiguous(), mask=up(mask.double())[0].float().contiguous(),
+                normal=up(normal).float().contiguous())
 
 
 def constant_targets(cam: Camera, rgb: float = 0.5, depth: float = 4.0) -> dict:

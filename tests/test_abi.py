@@ -69,3 +69,13 @@ def test_default_params_and_argument_errors_without_gpu():
     bad.capacity_pairs = 1 << 31
     assert L.pgs_scene_create(ctypes.byref(bad), ctypes.byref(h)) == B.PGS_ERR_INVALID_ARG
     assert L.pgs_status_string(B.PGS_ERR_TIMEOUT) == b"bounded wait timed out"
+
+
+def test_stage_names_match_header_enum():
+    src = open(os.path.join(ROOT, "include", "pgs.h")).read()
+    stages = dict((m.group(1).lower(), int(m.group(2)))
+                  for m in re.finditer(r"\bPGS_STAGE_([A-Z_0-9]+)\s*=\s*(\d+)", src))
+    n = int(re.search(r"\bPGS_N_STAGES\s*=\s*(\d+)", src).group(1))
+    assert len(B.STAGES) == n == len(stages)
+    for i, name in enumerate(B.STAGES):
+        assert stages[name] == i, name
