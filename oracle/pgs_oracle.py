@@ -885,7 +885,7 @@ def ncc_loss(cams_in: Sequence, maps: Sequence[dict], centers, geo: bool = True,
         li = ((1.0 - out["ncc"]) * out["valid"]).sum() / nv if nv > 0 else torch.zeros((), dtype=DT)
         total = total + li
         per.append(dict(ncc=out["ncc"].detach(), valid=out["valid"], amb=out["amb"], cell=out["cell"],
-                        n_valid=nv, loss=float(li)))
+                        n_valid=nv, loss=float(li.detach())))
     L = total / len(pairs) if pairs else total
     res = dict(loss=float(L), pairs=per)
     if grad and pairs:
