@@ -244,7 +244,8 @@ enum pgs_stage {
   PGS_STAGE_PROJECT_BWD = 7,  /* projection (+ decoder input/activation) backward */
   PGS_STAGE_WGRAD = 8,        /* decoder weight-gradient reduction */
   PGS_STAGE_PRIOR = 9,        /* enhanced depth prior (pgs_filter_depth_prior) */
-  PGS_N_STAGES = 10
+  PGS_STAGE_NCC = 10,         /* batch geometric NCC loss (pgs_ncc_loss_grad) */
+  PGS_N_STAGES = 11
 };
 pgs_status pgs_set_profiling(pgs_scene* s, int enable);
 pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);
@@ -299,6 +300,49 @@ pgs_status pgs_filter_depth_prior(pgs_scene* s, const pgs_camera* cams, int n_vi
                                   const float* d_points, int64_t n_points, const pgs_prior_params* pp,
                                   float* d_prior_out, float* d_mask_out, float* d_scale_shift, float* d_err_out,
                                   cudaStream_t stream);
+
+/* Batch geometric NCC loss (Step 3 of the batch-level progressive training,
+ * Sec. 3.4, Eq. 10) of a rendered batch, with its gradients.
+ *  - pairs: views (2i+1, 2i) for i < n_views / 2; view 2i+1 is the reference
+ *    whose patches are compared, view 2i the partner (an odd last view is
+ *    unpaired);
+ *  - d_centers: uint32 [n_views / 2][n_per_pair] patch centres drawn by the
+ *    caller (the random draw of Eq. 10), as local pixel indices y W + x of the
+ *    pair's reference view;
+ *  - each patch is the 7 x 7 block of reference pixels around its centre,
+ *    mapped into the partner by the homography of the plane through the
+ *    centre's back-projection (rendered D_hat) with the rendered normal N_hat
+ *    there; NCC = S_ab / sqrt((S_aa + eps)(S_bb + eps)) over the centred sums
+ *    of the BT.601 luma of the reference pixels (a) and of the partner read
+ *    bilinearly at the warped positions (b, pixel centres at +1/2);
+ *  - a patch is used when it lies inside the reference frame, D_hat > 0 and
+ *    |N_hat . K^-1 p~| >= 1e-8 at its centre, and every warped sample has the
+ *    plane in front of both cameras and its bilinear footprint inside the
+ *    partner frame; centres outside the reference view give unused patches;
+ *  - L_ncc = (1 / (n_views / 2)) sum over pairs of the mean of (1 - NCC) over
+ *    the pair's used patches (a pair without any adds 0).
+ * The partner's colours are under stop-gradient.  geometric = 1: the warped
+ * positions stay differentiable, so the gradient also reaches D_hat and N_hat
+ * at each patch centre; geometric = 0: the whole sampled partner patch is a
+ * constant and only the reference colours receive gradients.
+ * img: rgb, depth (D_hat) and normal (N_hat) of the rendered batch (other
+ * fields unused).  Outputs (device, caller-owned): d_ncc float[n_views / 2]
+ * [n_per_pair] the NCC of each patch, or -2 for an unused one (required: the
+ * kernels keep the validity of each patch there); d_loss float[2] =
+ * (lambda_ncc * L_ncc, L_ncc); gradients ACCUMULATED (+=) into grad->rgb of
+ * the reference views and, in the geometric form, grad->depth and
+ * grad->normal at the patch centres, scaled by lambda_ncc.  Call it after
+ * pgs_loss_grad (which overwrites the gradients) and before pgs_backward.
+ * Errors: PGS_ERR_INVALID_ARG for null pointers, n_per_pair outside
+ * 0..2^26, eps < 0. */
+typedef struct pgs_ncc_params {
+  float lambda_ncc;             /* weight of L_ncc in the total loss (0.2 at the end of the paper's schedule) */
+  float eps;                    /* added to each centred sum of squares (1e-6) */
+  int32_t geometric;            /* 1: gradients reach D_hat and N_hat through the warp; 0: colours only */
+} pgs_ncc_params;
+pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                             const uint32_t* d_centers, int64_t n_per_pair, const pgs_ncc_params* np,
+                             float* d_ncc, float* d_loss, const pgs_image_grad_ptrs* grad, cudaStream_t stream);
 
 /* The scene's current render parameters (as created, or as the autotuner set them). */
 pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out);

@@ -80,7 +80,7 @@ class LossParams:
 
 def _t(a) -> torch.Tensor:
     if isinstance(a, torch.Tensor):
-        return a.to(DT)
+        return a.cpu().to(DT)
     return torch.as_tensor(np.asarray(a), dtype=DT)
 
 
@@ -755,6 +755,11 @@ LUMA = (0.299, 0.587, 0.114)
 AMB_NCC_EDGE = 1e-3
 AMB_NCC_CELL = 1e-3
 AMB_NCC_FRONT = 1e-6    # relative: m . r_q or h_z this close to 0
+# Conditioning of the NCC of a patch under errors db in the partner samples:
+# |dNCC| <= sqrt((1 - NCC^2) / S_bb) |db|_2 (the gradient of NCC with respect
+# to b has that norm for eps -> 0), and |db|_2 <= 7 (max_k |grad b_k| du +
+# d_luma) for position errors du and luma rounding d_luma.  ``ncc_patches``
+# returns S_bb and max_k |grad b_k| so that a comparison can take that bound.
 
 
 def ncc_pairs(n_views: int) -> List[tuple]:
@@ -805,6 +810,21 @@ def _bilinear(img: torch.Tensor, x: torch.Tensor, y: torch.Tensor) -> torch.Tens
     a, b = img[j0, i0], img[j0, i0 + 1]
     c, d = img[j0 + 1, i0], img[j0 + 1, i0 + 1]
     return (1 - aw) * ((1 - au) * a + au * b) + aw * ((1 - au) * c + au * d)
+
+
+def _bilinear_slope(img: torch.Tensor, x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
+    """|grad| of the bilinear interpolant of img at pixel coordinates (per-cell slopes)."""
+    H, W = img.shape
+    u, w = x - 0.5, y - 0.5
+    fu, fw = torch.floor(u), torch.floor(w)
+    i0 = fu.clamp(0, W - 2).long()
+    j0 = fw.clamp(0, H - 2).long()
+    au, aw = u - fu, w - fw
+    a, b = img[j0, i0], img[j0, i0 + 1]
+    c, d = img[j0 + 1, i0], img[j0 + 1, i0 + 1]
+    gx = (1 - aw) * (b - a) + aw * (d - c)
+    gy = (1 - au) * (c - a) + au * (d - b)
+    return torch.sqrt(gx * gx + gy * gy)
 
 
 def ncc(a: torch.Tensor, b: torch.Tensor, eps: float = NCC_EPS) -> torch.Tensor:
@@ -860,10 +880,14 @@ def ncc_patches(cr: dict, cs: dict, ref: dict, part_rgb: torch.Tensor, centers: 
     else:
         b = _bilinear(g, ux.detach(), uy.detach()).detach()
     val = ncc(a, b, eps)
+    bd = b.detach()
+    sbb = ((bd - bd.mean(-1, keepdim=True)) ** 2).sum(-1)
+    slope = _bilinear_slope(g, ux.detach(), uy.detach()).amax(1)
     scale_mr = mr.detach().abs().amax(1).clamp(min=1e-30)
     amb = plane & (near | (mr.detach().abs() < AMB_NCC_FRONT * scale_mr.unsqueeze(1))
                    | (h[..., 2].detach().abs() < AMB_NCC_FRONT * h[..., 2].detach().abs().amax(1, keepdim=True))).any(1)
-    return dict(ncc=val, valid=valid, amb=amb, cell=plane & cell.any(1), warped=torch.stack([ux, uy], -1))
+    return dict(ncc=val, valid=valid, amb=amb, cell=plane & cell.any(1), warped=torch.stack([ux, uy], -1),
+                sbb=sbb, slope=slope)
 
 
 def ncc_loss(cams_in: Sequence, maps: Sequence[dict], centers, geo: bool = True, eps: float = NCC_EPS,
@@ -885,9 +909,9 @@ def ncc_loss(cams_in: Sequence, maps: Sequence[dict], centers, geo: bool = True,
         li = ((1.0 - out["ncc"]) * out["valid"]).sum() / nv if nv > 0 else torch.zeros((), dtype=DT)
         total = total + li
         per.append(dict(ncc=out["ncc"].detach(), valid=out["valid"], amb=out["amb"], cell=out["cell"],
-                        n_valid=nv, loss=float(li.detach())))
+                        sbb=out["sbb"], slope=out["slope"], n_valid=nv, loss=float(li.detach())))
     L = total / len(pairs) if pairs else total
-    res = dict(loss=float(L), pairs=per)
+    res = dict(loss=float(L.detach()), pairs=per)
     if grad and pairs:
         (lam * L).backward()
         res["grads"] = [{k: (lf[k].grad if lf[k].grad is not None else torch.zeros_like(lf[k])).detach()

@@ -107,6 +107,10 @@ class PriorParams(C.Structure):
     _fields_ = [("tau_d", C.c_float), ("k_neighbors", C.c_int32)]
 
 
+class NccParams(C.Structure):
+    _fields_ = [("lambda_ncc", C.c_float), ("eps", C.c_float), ("geometric", C.c_int32)]
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("blend_batch", C.c_int32), ("ms", C.c_float)]
 
@@ -116,9 +120,9 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
-                "pgs_scene_get_params", "pgs_filter_depth_prior")
+                "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad",
-          "prior")
+          "prior", "ncc")
 
 
 def _declare(L: C.CDLL) -> None:
@@ -157,6 +161,8 @@ def _declare(L: C.CDLL) -> None:
                                P(TuneEntry), i32, P(i32), vp]
     L.pgs_scene_get_params.argtypes = [vp, P(RenderParams)]
     L.pgs_filter_depth_prior.argtypes = [vp, P(Camera), i32, vp, vp, i64, P(PriorParams), vp, vp, vp, vp, vp]
+    L.pgs_ncc_loss_grad.argtypes = [vp, P(Camera), i32, P(ImagePtrs), vp, i64, P(NccParams), vp, vp,
+                                    P(ImageGradPtrs), vp]
 
 
 def check(status: int) -> None:
@@ -387,6 +393,27 @@ class Scene:
                                            pts.shape[0], C.byref(pp), _ptr(out["prior"]), _ptr(out["mask"]),
                                            _ptr(out["scale_shift"]), _ptr(out["err"]), _stream(stream)))
         return out
+
+    def ncc_loss_grad(self, cams, images: "Images", centers: torch.Tensor, grads: "ImageGrads",
+                      lambda_ncc: float = 0.2, eps: float = 1e-6, geometric: bool = True,
+                      ncc_out: Optional[torch.Tensor] = None, loss: Optional[torch.Tensor] = None, stream=None,
+                      packed=None) -> dict:
+        """Batch geometric NCC loss (pgs_ncc_loss_grad, Eq. 10): centres int32/uint32 [B/2, N] local
+        pixel indices of the reference views; gradients accumulated into `grads`.  Returns
+        dict(ncc [B/2, N] (-2 = unused patch), loss [2] = (lambda * L, L))."""
+        cc = packed if packed is not None else pack_cameras(cams)
+        centers = centers.contiguous()
+        n_pairs = len(cams) // 2
+        n_per = centers.shape[-1] if centers.numel() else 0
+        if ncc_out is None:
+            ncc_out = torch.empty(max(1, n_pairs * n_per), device=images.rgb.device)
+        if loss is None:
+            loss = torch.zeros(2, device=images.rgb.device)
+        npar = NccParams(lambda_ncc, eps, 1 if geometric else 0)
+        check(lib().pgs_ncc_loss_grad(self.handle, cc, len(cams), C.byref(images.ptrs()),
+                                      _ptr(centers) if centers.numel() else None, n_per, C.byref(npar),
+                                      _ptr(ncc_out), _ptr(loss), C.byref(grads.ptrs()), _stream(stream)))
+        return dict(ncc=ncc_out[:n_pairs * n_per].view(n_pairs, n_per), loss=loss)
 
     def params(self) -> dict:
         p = RenderParams()

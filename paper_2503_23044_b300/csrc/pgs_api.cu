@@ -93,6 +93,7 @@ struct pgs_scene {
   uint32_t *order_k = nullptr, *order_v = nullptr, *order_kb = nullptr, *order_vb = nullptr;  // tile queue
   uint32_t* queue_ctr = nullptr;         // [0] forward, [1] backward
   float *prior_partials = nullptr, *prior_means = nullptr;   // enhanced depth prior fit
+  int* ncc_counts = nullptr;                                  // used patches per NCC pair
   uint32_t *cull_flags = nullptr, *cull_offs = nullptr, *rows = nullptr;
   float *sc_dZ = nullptr, *sc_H = nullptr, *sc_dH = nullptr, *sc_X = nullptr, *wg_partials = nullptr;
   int wg_blocks = 0;
@@ -166,7 +167,7 @@ void pgs_scene_destroy(pgs_scene* s) {
                 s->ptile_b, s->pg_a, s->pg_b, s->ranges, s->cull_flags, s->cull_offs, s->rows, s->sc_dZ, s->sc_H,
                 s->sc_dH, s->sc_X, s->wg_partials, s->d_cnt, s->d_tot, s->scan_sums, s->sort_mem, s->d_flags,
                 s->loss_counts, s->loss_partials, s->order_k, s->order_v, s->order_kb, s->order_vb,
-                s->queue_ctr, s->prior_partials, s->prior_means};
+                s->queue_ctr, s->prior_partials, s->prior_means, s->ncc_counts};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : s->ev)
@@ -236,6 +237,7 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   ALLOC(s->queue_ctr, 2);
   ALLOC(s->prior_partials, (long long)kMaxViews * kPriorBlocks * 3);
   ALLOC(s->prior_means, (long long)kMaxViews * 4);
+  ALLOC(s->ncc_counts, kMaxViews / 2);
   ALLOC(s->d_cnt, 8);
   ALLOC(s->d_tot, 4);
   ALLOC(s->scan_sums, kScanBlocks);
@@ -578,6 +580,34 @@ pgs_status pgs_filter_depth_prior(pgs_scene* s, const pgs_camera* cams, int n_vi
                       d_scale_shift, d_prior_out, d_mask_out, d_err_out, s->num_sms, st);
   s->launches += kPriorLaunches;
   prof_mark(s, PGS_STAGE_PRIOR, 1, st);
+  PGS_CUDA(cudaGetLastError());
+  return PGS_OK;
+}
+
+pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
+                             const uint32_t* d_centers, int64_t n_per_pair, const pgs_ncc_params* np, float* d_ncc,
+                             float* d_loss, const pgs_image_grad_ptrs* grad, cudaStream_t st) {
+  if (!s || !img || !np || !d_loss || !grad) return fail(PGS_ERR_INVALID_ARG, "null argument");
+  if (!img->rgb || !img->depth || !img->normal || !grad->rgb || (np->geometric && (!grad->depth || !grad->normal)))
+    return fail(PGS_ERR_INVALID_ARG, "null image or gradient pointer");
+  if (n_per_pair < 0 || n_per_pair > (int64_t(1) << 26)) return fail(PGS_ERR_INVALID_ARG, "n_per_pair %lld",
+                                                                    (long long)n_per_pair);
+  if (!(np->eps >= 0.f) || !std::isfinite(np->lambda_ncc)) return fail(PGS_ERR_INVALID_ARG, "eps or lambda_ncc");
+  BatchDev b;
+  pgs_status r = build_batch(s, cams, n_views, b);
+  if (r) return r;
+  const int n_pairs = n_views / 2;
+  if (n_pairs > 0 && n_per_pair > 0 && (!d_centers || !d_ncc))
+    return fail(PGS_ERR_INVALID_ARG, "null centres or NCC output");
+  NccArgs a;
+  a.lambda = np->lambda_ncc;
+  a.eps = np->eps;
+  a.geometric = np->geometric ? 1 : 0;
+  prof_mark(s, PGS_STAGE_NCC, 0, st);
+  launch_ncc(b, a, d_centers, (long long)n_per_pair, n_pairs, img->rgb, img->depth, img->normal, d_ncc, d_loss,
+             grad->rgb, grad->depth, grad->normal, s->ncc_counts, s->num_sms, st);
+  s->launches += (n_pairs > 0 && n_per_pair > 0) ? kNccLaunches : 1;
+  prof_mark(s, PGS_STAGE_NCC, 1, st);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;
 }

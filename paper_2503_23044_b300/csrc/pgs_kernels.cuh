@@ -9,6 +9,14 @@ constexpr int kLossBlocks = 1184;  // 8 x 148 SMs
 // kernels enqueued by the multi-kernel launch helpers
 constexpr int kScanLaunches = 3, kLossLaunches = 3, kWgradLaunches = 2;
 constexpr int kPriorBlocks = 64, kPriorLaunches = 5, kPriorMaxK = 4;
+constexpr int kNccLaunches = 3;
+constexpr float kNccInvalid = -2.f;   // NCC of a patch that is not used (NCC itself lies in [-1, 1])
+
+// batch geometric NCC: weight of the loss, the variance guard and the stop-gradient form
+struct NccArgs {
+  float lambda, eps;
+  int geometric;
+};
 
 // enhanced depth prior: the k nearest batch views of each view (-1 = none) and the filter threshold
 struct PriorArgs {
@@ -93,6 +101,9 @@ __host__ __device__ __forceinline__ size_t sc_at(long long r, int f, int width) 
 __host__ __device__ __forceinline__ long long sc_rows(long long cap) { return (cap + kScBlock - 1) / kScBlock * kScBlock; }
 
 // k_prior.cu
+void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
+                const float* rgb, const float* depth, const float* normal, float* ncc, float* loss, float* g_rgb,
+                float* g_depth, float* g_normal, int* counts, int num_sms, cudaStream_t st);
 void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp, const float* pts, long long n_pts,
                          float* partials, float* means, float* scale_shift, float* prior_out, float* mask_out,
                          float* err_out, int num_sms, cudaStream_t st);

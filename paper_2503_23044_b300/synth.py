@@ -228,7 +228,13 @@ def aerial_cameras(rng, terrain: Terrain, extent: float, resolutions, altitude: 
         centers = [((i + 0.5) / gx * extent - extent / 2.0, (j + 0.5) / gy * extent - extent / 2.0)
                    for j in range(gy) for i in range(gx)]
         pitches = [math.radians(rng.uniform(*pitch_deg)) for _ in centers]
-        yaws = [rng.uniform(0.0, 2 * math.pi) for _ in centers]
+        # views 2i and 2i+1 (neighbours on the grid) fly the same heading within
+        # +-15 degrees, like consecutive frames of a sweep, so the view pairs of the
+        # batch overlap
+        yaws = []
+        for k in range(len(centers)):
+            yaws.append(rng.uniform(0.0, 2 * math.pi) if k % 2 == 0 else
+                        yaws[-1] + rng.uniform(-math.pi / 12.0, math.pi / 12.0))
     for (cx, cy), p, yw, (w, h) in zip(centers, pitches, yaws, resolutions):
         ground = float(terrain.height(np.array(cx), np.array(cy)))
         cams.append(look_camera((cx, cy, ground + altitude), yw, p, w, h))
