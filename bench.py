@@ -2,10 +2,11 @@
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pgs|reference]
 
-A step is one pass of the whole hot path over one batch: LoD/frustum cull,
-decoder, projection, depth sort, tile binning, tile sort, forward blend,
-losses, backward blend, projection/decoder backward and the decoder's weight
-gradients.  Workload: 8 aerial views of 1600x1064 over 200k anchors (2M
+A step is one pass of the whole hot path over one batch: the enhanced depth
+prior of the batch (Step 2), LoD/frustum cull, decoder, projection, depth sort,
+tile binning, tile sort, forward blend, losses, the batch geometric NCC of the
+view pairs (Step 3, Eq. 10), backward blend, projection/decoder backward and
+the decoder's weight gradients.  Workload: 8 aerial views of 1600x1064 over 200k anchors (2M
 neural Gaussians) on a 3-level LoD hierarchy, seeded synthetic terrain.
 
 Batched form (the headline): all views in one call sequence, captured once in
@@ -115,6 +116,8 @@ def resolution_desc(cams) -> str:
 
 
 N_SPARSE = 50_000   # sparse-cloud stand-in for the depth-prior scale/shift fit
+N_PATCH = 65_536    # patch centres per view pair for the batch geometric NCC (Eq. 10)
+LAMBDA_NCC = 0.2    # NCC weight at the end of the paper's schedule
 
 
 def make_workload(name: str, seed: int, device: str):
@@ -194,6 +197,22 @@ def cpu_prior_seconds(sc, pseudo):
     return time.perf_counter() - t0
 
 
+NCC_SAMPLE = 4096   # oracle NCC patches per pair timed; the cost is scaled to N_PATCH
+
+
+def cpu_ncc_seconds(sc, maps):
+    """FP64 oracle of the batch's NCC loss and gradients on NCC_SAMPLE patches per
+    pair (seeded centres), scaled to N_PATCH patches per pair: seconds."""
+    import oracle as O
+    cams = sc["cameras"]
+    gen = torch.Generator().manual_seed(7)
+    centers = [torch.randperm(cams[2 * i + 1].width * cams[2 * i + 1].height, generator=gen)[:NCC_SAMPLE].numpy()
+               for i in range(len(cams) // 2)]
+    t0 = time.perf_counter()
+    O.ncc_loss(cams, maps, centers, geo=True, lam=LAMBDA_NCC)
+    return (time.perf_counter() - t0) * N_PATCH / NCC_SAMPLE
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -204,21 +223,23 @@ def run_reference(args):
     V = len(sc["cameras"])
     # the batch's pseudo depths from a stride-4 march (values held over 4x4 blocks: the
     # oracle filter's cost per pixel does not depend on them) and the sparse cloud
-    pseudo = [synth.pseudo_depth(tg["depth"], tg["mask"] > 0, seed=i)[0]
-              for i, tg in enumerate(synth.march_targets(sc["terrain"], c, stride=4, seed=i) for c in sc["cameras"])]
+    marched = [synth.march_targets(sc["terrain"], c, stride=4, seed=i) for i, c in enumerate(sc["cameras"])]
+    pseudo = [synth.pseudo_depth(tg["depth"], tg["mask"] > 0, seed=i)[0] for i, tg in enumerate(marched)]
     sc["sparse"] = synth.sparse_points(sc["terrain"], sc["extent"], N_SPARSE, seed=0)
     t_prior = cpu_prior_seconds(sc, pseudo)
+    t_ncc = cpu_ncc_seconds(sc, marched)
     per_step = []
     for s in range(args.warmup + args.steps):
         vps, _ = cpu_views_per_s(sc, None, [s % V])
-        per_step.append(1.0 / vps + t_prior / V)
+        per_step.append(1.0 / vps + (t_prior + t_ncc) / V)
     timed = per_step[args.warmup:]
     value = len(timed) / sum(timed)
     cores = torch.get_num_threads()
     sample = (f"per step one of the {V} views ({resolution_desc(sc['cameras'])}): FP64 decode+projection of every "
               "LoD-active anchor, then a "
               f"{CPU_CROP}x{CPU_CROP} crop fwd+bwd; per-pixel cost extrapolated to the full frame; plus 1/{V} of the "
-              f"batch's FP64 enhanced depth-prior filter ({t_prior:.2f} s for all views, timed once)")
+              f"batch's FP64 enhanced depth-prior filter ({t_prior:.2f} s for all views, timed once) and of its FP64 "
+              f"NCC loss + gradients ({NCC_SAMPLE} patches per pair timed once, scaled to {N_PATCH}: {t_ncc:.2f} s)")
     line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
                 ms_per_step=1e3 * sum(timed) / len(timed), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
@@ -231,6 +252,16 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ GPU arm
+def arena_slice(B, img, grads, v0: int, v1: int):
+    """Images and image gradients of views v0 .. v1 - 1 as views of a batch arena."""
+    a, b = img.offsets[v0], img.offsets[v1]
+    s1 = lambda x: None if x is None else x[a:b]
+    s3 = lambda x: x[3 * a:3 * b]
+    im = B.Images(s3(img.rgb), s1(img.depth), s3(img.normal), s1(img.dist), s1(img.t_final), s1(img.last),
+                  s1(img.n_contrib), s1(img.n_eval), [o - a for o in img.offsets[v0:v1 + 1]], img.shapes[v0:v1])
+    return im, B.ImageGrads(s3(grads.rgb), s1(grads.depth), s3(grads.normal))
+
+
 def run_pgs(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -258,6 +289,12 @@ def run_pgs(args):
     n_pix = images.offsets[-1]
     grads = B.ImageGrads.empty(n_pix, device=device)
     loss = torch.zeros(4, device=device)
+    # NCC patch centres: a seeded draw (without repetition) over each pair's reference view
+    gen = torch.Generator().manual_seed(1000 + rank)
+    centers = torch.stack([torch.randperm(cams[2 * i + 1].width * cams[2 * i + 1].height, generator=gen)[:N_PATCH]
+                           for i in range(V // 2)]).to(torch.int32).to(device)
+    ncc_buf = torch.empty(max(1, centers.numel()), device=device)
+    ncc_loss = torch.zeros(2, device=device)
     stream = torch.cuda.Stream(device=device)
 
     def step():
@@ -265,6 +302,9 @@ def run_pgs(args):
         scene.filter_depth_prior(cams, pseudo, sparse, tau_d=1.0, k_neighbors=2, packed=packed, out=prior_out)
         scene.render(cams, images, packed=packed)
         scene.loss_grad(cams, images, targets, loss=loss, grads=grads, packed=packed)
+        # batch geometric NCC (Step 3): pairs (2i+1, 2i), gradients added to the image gradients
+        scene.ncc_loss_grad(cams, images, centers, grads, lambda_ncc=LAMBDA_NCC, ncc_out=ncc_buf, loss=ncc_loss,
+                            packed=packed)
         for v in pg.values():
             v.zero_()
         scene.backward(cams, images, grads, pg, packed=packed)
@@ -352,7 +392,12 @@ def run_pgs(args):
     if not args.no_plain:
         pscene, _, _ = build_scene(sc, B, device, 1 << 26, len(sc["x"]), B.DECODE_FP32)
         pscene.bind_anchors(t["x"], t["level"], t["log_l"], t["offsets"], t["feat"], t["W1"], t["b1"], t["W2"], t["b2"])
-        pimgs = [B.Images.empty([c], device=device) for c in cams]
+        pimg_all = B.Images.empty(cams, device=device)
+        pgr_all = B.ImageGrads.empty(pimg_all.offsets[-1], device=device)
+        pimgs, pgr = zip(*[arena_slice(B, pimg_all, pgr_all, v, v + 1) for v in range(V)])
+        ppairs = [arena_slice(B, pimg_all, pgr_all, 2 * i, 2 * i + 2) for i in range(V // 2)]
+        pkp = [B.pack_cameras(cams[2 * i:2 * i + 2]) for i in range(V // 2)]
+        pncc = torch.empty_like(ncc_buf)
         # per-view targets as slices of batch buffers, so the batch-level depth-prior
         # filter writes every view's prior and mask in one call
         pbatch = B.Targets(targets.rgb.clone(), torch.empty_like(targets.prior), torch.empty_like(targets.mask))
@@ -362,7 +407,6 @@ def run_pgs(args):
             n = c.width * c.height
             ptg.append(B.Targets(pbatch.rgb[3 * off:3 * (off + n)], pbatch.prior[off:off + n], pbatch.mask[off:off + n]))
             off += n
-        pgr = [B.ImageGrads.empty(c.width * c.height, device=device) for c in cams]
         pk = [B.pack_cameras([c]) for c in cams]
 
         def plain_step():
@@ -370,6 +414,11 @@ def run_pgs(args):
             for i, c in enumerate(cams):
                 pscene.render([c], pimgs[i], packed=pk[i])
                 pscene.loss_grad([c], pimgs[i], ptg[i], loss=loss, grads=pgr[i], packed=pk[i])
+                if i % 2 == 1:      # reference view of the pair (i, i - 1), whose partner is rendered
+                    q = i // 2
+                    pscene.ncc_loss_grad(cams[i - 1:i + 1], ppairs[q][0], centers[q:q + 1], ppairs[q][1],
+                                         lambda_ncc=LAMBDA_NCC, ncc_out=pncc[q * N_PATCH:(q + 1) * N_PATCH],
+                                         loss=ncc_loss, packed=pkp[q])
                 pscene.backward([c], pimgs[i], pgr[i], pg, packed=pk[i])
 
         with torch.cuda.stream(stream):
@@ -394,7 +443,7 @@ def run_pgs(args):
     # end to end through the public API: targets from pinned host memory in,
     # loss scalars out, every step
     host_t = [x.cpu().pin_memory() for x in (targets.rgb, pseudo)]
-    host_loss = torch.zeros(4).pin_memory()
+    host_loss = torch.zeros(6).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_t)
     d2h = host_loss.numel() * 4
     ke = max(1, min(args.steps, 10))
@@ -408,7 +457,8 @@ def run_pgs(args):
             targets.rgb.copy_(host_t[0], non_blocking=True)
             pseudo.copy_(host_t[1], non_blocking=True)
             run()
-            host_loss.copy_(loss, non_blocking=True)
+            host_loss[:4].copy_(loss, non_blocking=True)
+            host_loss[4:].copy_(ncc_loss, non_blocking=True)
             e1.record(stream)
         e1.synchronize()
         em += e0.elapsed_time(e1)
@@ -417,7 +467,7 @@ def run_pgs(args):
     # roofline of the dominant kernel
     peaks = _peaks()
     dom = max(("blend_bwd", "blend_fwd", "tile_sort", "depth_sort", "project", "project_bwd", "wgrad", "bin", "loss",
-               "prior"),
+               "prior", "ncc"),
               key=lambda k: stage_ms.get(k, 0.0))
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
@@ -443,12 +493,15 @@ def run_pgs(args):
         torch.set_num_threads(max(1, len(os.sched_getaffinity(0))))
         vps, parts = cpu_views_per_s(sc, tviews, list(range(V)))
         t_prior = cpu_prior_seconds(sc, [tv["pseudo"] for tv in tviews])
-        vps = V / (V / vps + t_prior)
+        t_ncc = cpu_ncc_seconds(sc, [{k: tv[k].cpu() for k in ("rgb", "depth", "normal")} for tv in tviews])
+        vps = V / (V / vps + t_prior + t_ncc)
         cpu = dict(value=vps, unit="views/s", cores=torch.get_num_threads(), kind="oracle",
                    sample=f"all {V} views: the batch's FP64 enhanced depth-prior filter, FP64 decode+projection of "
-                          f"every LoD-active anchor, then one {CPU_CROP}x{CPU_CROP} crop fwd+bwd per view; per-pixel "
-                          "cost of the crops extrapolated to the full frame",
-                   seconds=dict(prior=t_prior, setup=sum(p[0] for p in parts), crops=sum(p[1] for p in parts)))
+                          f"every LoD-active anchor, then one {CPU_CROP}x{CPU_CROP} crop fwd+bwd per view (per-pixel "
+                          f"cost extrapolated to the full frame), and the FP64 NCC loss + gradients on {NCC_SAMPLE} "
+                          f"patches per pair (cost scaled to {N_PATCH}) on the synthetic colour, depth and normal maps",
+                   seconds=dict(prior=t_prior, ncc_scaled=t_ncc, setup=sum(p[0] for p in parts),
+                                crops=sum(p[1] for p in parts)))
 
     clocks = clk.summary()
     if rank == 0:
@@ -463,6 +516,8 @@ def run_pgs(args):
                                 if tune else "off",
                                 depth_prior=f"enhanced filter every step (Step 2): {N_SPARSE} sparse points, k=2 "
                                             "nearest views, tau_d=1 px -> the loss's prior and mask",
+                                ncc=f"batch geometric NCC every step (Step 3, Eq. 10): {V // 2} view pairs x {N_PATCH} "
+                                    f"7x7 patches (seeded centres), lambda={LAMBDA_NCC}, geometric gradients",
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"replicas x{world}"),
                     plain=dict(value=plain_vps, unit="views/s", form="batch depth-prior filter, then one view per call "
