@@ -64,12 +64,6 @@ __device__ __forceinline__ void stage_record(BlendSmem<NB>& s, int slot, const f
   s.n[slot] = r.n;
 }
 
-__device__ __forceinline__ float rcp_approx(float x) {
-  float y;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
 // power of the Gaussian at the pixel, with the exact operation order shared by both passes
 __device__ __forceinline__ float eval_power(const float4 q, float dx, float dy) {
   return __fmaf_rn(q.x, __fmul_rn(dx, dx), __fmaf_rn(q.z, __fmul_rn(dy, dy), __fmul_rn(q.y, __fmul_rn(dx, dy))));

@@ -93,7 +93,8 @@ struct pgs_scene {
   uint32_t *order_k = nullptr, *order_v = nullptr, *order_kb = nullptr, *order_vb = nullptr;  // tile queue
   uint32_t* queue_ctr = nullptr;         // [0] forward, [1] backward
   float *prior_partials = nullptr, *prior_means = nullptr;   // enhanced depth prior fit
-  int* ncc_counts = nullptr;                                  // used patches per NCC pair
+  void* ncc_scratch = nullptr;                                // NCC per-pair counts, means, relative poses
+  float* ncc_luma = nullptr;                                  // NCC: luma of the paired views [max_pixels]
   uint32_t *cull_flags = nullptr, *cull_offs = nullptr, *rows = nullptr;
   float *sc_dZ = nullptr, *sc_H = nullptr, *sc_dH = nullptr, *sc_X = nullptr, *wg_partials = nullptr;
   int wg_blocks = 0;
@@ -167,7 +168,7 @@ void pgs_scene_destroy(pgs_scene* s) {
                 s->ptile_b, s->pg_a, s->pg_b, s->ranges, s->cull_flags, s->cull_offs, s->rows, s->sc_dZ, s->sc_H,
                 s->sc_dH, s->sc_X, s->wg_partials, s->d_cnt, s->d_tot, s->scan_sums, s->sort_mem, s->d_flags,
                 s->loss_counts, s->loss_partials, s->order_k, s->order_v, s->order_kb, s->order_vb,
-                s->queue_ctr, s->prior_partials, s->prior_means, s->ncc_counts};
+                s->queue_ctr, s->prior_partials, s->prior_means, s->ncc_scratch, s->ncc_luma};
   for (void* p : ps)
     if (p) cudaFree(p);
   for (auto& e : s->ev)
@@ -237,7 +238,8 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   ALLOC(s->queue_ctr, 2);
   ALLOC(s->prior_partials, (long long)kMaxViews * kPriorBlocks * 3);
   ALLOC(s->prior_means, (long long)kMaxViews * 4);
-  ALLOC(s->ncc_counts, kMaxViews / 2);
+  if (e == cudaSuccess) e = cudaMalloc(&s->ncc_scratch, ncc_scratch_bytes());
+  ALLOC(s->ncc_luma, d.max_pixels);
   ALLOC(s->d_cnt, 8);
   ALLOC(s->d_tot, 4);
   ALLOC(s->scan_sums, kScanBlocks);
@@ -605,8 +607,8 @@ pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, 
   a.geometric = np->geometric ? 1 : 0;
   prof_mark(s, PGS_STAGE_NCC, 0, st);
   launch_ncc(b, a, d_centers, (long long)n_per_pair, n_pairs, img->rgb, img->depth, img->normal, d_ncc, d_loss,
-             grad->rgb, grad->depth, grad->normal, s->ncc_counts, s->num_sms, st);
-  s->launches += (n_pairs > 0 && n_per_pair > 0) ? kNccLaunches : 1;
+             grad->rgb, grad->depth, grad->normal, s->ncc_scratch, s->ncc_luma, s->num_sms, st);
+  s->launches += (n_pairs > 0 && n_per_pair > 0) ? kNccLaunches : 0;
   prof_mark(s, PGS_STAGE_NCC, 1, st);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;

@@ -73,6 +73,13 @@ __device__ __forceinline__ int view_of_pixel(const BatchDev& b, long long p) {
   return v;
 }
 
+// 1/x with the hardware approximation (about 1 ulp), denormals flushed
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -181,7 +188,7 @@ struct TileRows {
   float dy_left, dy_right;
 };
 __device__ __forceinline__ TileRows tile_rows(const TileEllipse& e, const ViewDev& v, int TW, int TH) {
-  const float cy = v.cy, cx = v.cx;
+  const float cy = v.cy;
   float my_abs = __fadd_rn(__fadd_rn(e.myh, e.myl), cy);
   float y_lo = __fsub_rn(my_abs, e.ry), y_hi = __fadd_rn(my_abs, e.ry);
   // float -> int conversions are clamped first (huge ellipses would saturate)

@@ -9,7 +9,9 @@ constexpr int kLossBlocks = 1184;  // 8 x 148 SMs
 // kernels enqueued by the multi-kernel launch helpers
 constexpr int kScanLaunches = 3, kLossLaunches = 3, kWgradLaunches = 2;
 constexpr int kPriorBlocks = 64, kPriorLaunches = 5, kPriorMaxK = 4;
-constexpr int kNccLaunches = 3;
+constexpr int kNccLaunches = 4;
+constexpr int kNccDone = kMaxViews / 2;   // index of the finished-blocks counter after the per-pair counts
+constexpr int kNccChunks = 16;            // loss-reduction blocks per pair
 constexpr float kNccInvalid = -2.f;   // NCC of a patch that is not used (NCC itself lies in [-1, 1])
 
 // batch geometric NCC: weight of the loss, the variance guard and the stop-gradient form
@@ -103,7 +105,8 @@ __host__ __device__ __forceinline__ long long sc_rows(long long cap) { return (c
 // k_prior.cu
 void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
                 const float* rgb, const float* depth, const float* normal, float* ncc, float* loss, float* g_rgb,
-                float* g_depth, float* g_normal, int* counts, int num_sms, cudaStream_t st);
+                float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms, cudaStream_t st);
+size_t ncc_scratch_bytes();
 void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp, const float* pts, long long n_pts,
                          float* partials, float* means, float* scale_shift, float* prior_out, float* mask_out,
                          float* err_out, int num_sms, cudaStream_t st);
