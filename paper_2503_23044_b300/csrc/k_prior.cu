@@ -117,18 +117,19 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
                                                       const float* __restrict__ scale_shift,
                                                       float* __restrict__ prior_out, float* __restrict__ mask_out,
                                                       float* __restrict__ err_out) {
+  int vi = 0;   // threads walk increasing pixel indices, so the view only moves forward
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < b.total_pixels;
        p += (long long)gridDim.x * blockDim.x) {
-    const int vi = view_of_pixel(b, p);
+    while (vi + 1 < b.n_views && p >= b.v[vi + 1].pix_off) ++vi;
     const ViewDev& va = b.v[vi];
-    const long long l = p - va.pix_off;
-    const int py = (int)(l / va.W), px = (int)(l - (long long)py * va.W);
+    const unsigned l = (unsigned)(p - va.pix_off);
+    const int py = (int)(l / (unsigned)va.W), px = (int)(l - (unsigned)py * (unsigned)va.W);
     const float raw = __ldg(dp + p);
     const float d = fmaf(scale_shift[2 * vi], raw, scale_shift[2 * vi + 1]);
     float keep_d = 0.f, keep = 0.f, E = -1.f;
     if (raw > 0.f && d > 0.f) {
       const float ux = (float)px + 0.5f, uy = (float)py + 0.5f;
-      const float ca[3] = {d * (ux - va.cx) / va.fx, d * (uy - va.cy) / va.fy, d};
+      const float ca[3] = {d * (ux - va.cx) * rcp_approx(va.fx), d * (uy - va.cy) * rcp_approx(va.fy), d};
       float xw[3];
       to_world(va, ca, xw);
       float best = 3.4e38f;
@@ -140,17 +141,19 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
         float cb[3];
         to_cam(vb, xw, cb);
         if (!(cb[2] > b.p.near_plane)) continue;
-        const float qx = vb.fx * cb[0] / cb[2] + vb.cx, qy = vb.fy * cb[1] / cb[2] + vb.cy;
+        const float izb = rcp_approx(cb[2]);
+        const float qx = fmaf(vb.fx * cb[0], izb, vb.cx), qy = fmaf(vb.fy * cb[1], izb, vb.cy);
         float rb;
         if (!prior_bilinear(dp, vb, qx, qy, rb)) continue;
         const float db = fmaf(scale_shift[2 * nb], rb, scale_shift[2 * nb + 1]);
         if (!(db > 0.f)) continue;
-        const float cb2[3] = {db * (qx - vb.cx) / vb.fx, db * (qy - vb.cy) / vb.fy, db};
+        const float cb2[3] = {db * (qx - vb.cx) * rcp_approx(vb.fx), db * (qy - vb.cy) * rcp_approx(vb.fy), db};
         float xw2[3], ca2[3];
         to_world(vb, cb2, xw2);
         to_cam(va, xw2, ca2);
         if (!(ca2[2] > b.p.near_plane)) continue;
-        const float rx = va.fx * ca2[0] / ca2[2] + va.cx - ux, ry = va.fy * ca2[1] / ca2[2] + va.cy - uy;
+        const float iza = rcp_approx(ca2[2]);
+        const float rx = fmaf(va.fx * ca2[0], iza, va.cx) - ux, ry = fmaf(va.fy * ca2[1], iza, va.cy) - uy;
         best = fminf(best, sqrtf(rx * rx + ry * ry));
         checked = true;
       }
