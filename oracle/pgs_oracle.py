@@ -917,3 +917,80 @@ def ncc_loss(cams_in: Sequence, maps: Sequence[dict], centers, geo: bool = True,
         res["grads"] = [{k: (lf[k].grad if lf[k].grad is not None else torch.zeros_like(lf[k])).detach()
                          for k in ("rgb", "depth", "normal")} for lf in leaves]
     return res
+
+
+# ------------------------------------------------------------------ TSDF fusion of rendered depth (supplementary)
+# The supplementary fuses rendered colour and depth maps into a projective TSDF
+# volume (Zeng et al.'s fusion; voxel 0.01 and truncation 0.04 for the aerial
+# scenes).  Reading of the steps, which the paper does not spell out:
+# * volume: an axis-aligned grid, voxel (i, j, k) centred at origin + (i + 1/2,
+#   j + 1/2, k + 1/2) * voxel, x fastest in memory;
+# * a voxel centre X is projected into each view in batch order: camera point
+#   R X + t with depth z > near, pixel (floor(u), floor(v)) of u = fx x / z + cx,
+#   v = fy y / z + cy (pixel centres at +1/2, so the nearest pixel), inside the
+#   frame, with a rendered depth D > 0 there;
+# * projective signed distance sdf = D - z; views with sdf < -trunc (behind the
+#   surface beyond the band) leave the voxel alone; otherwise the observation
+#   tsdf = min(1, sdf / trunc) enters a running average with unit weight,
+#   T <- (T W + tsdf) / (W + 1), W <- W + 1, and the pixel's colour likewise.
+AMB_TSDF_PIX = 1e-3     # px: a projection this close to a pixel boundary may pick the neighbour in FP32
+AMB_TSDF_SDF = 1e-5     # sdf this close to -trunc may fall on either side in FP32
+AMB_TSDF_NEAR = 1e-6    # relative: depth this close to the near plane
+
+
+def voxel_centres(origin, voxel: float, dims, index=None) -> torch.Tensor:
+    """World centres [n, 3] of the voxels with linear indices `index` (default all),
+    x fastest."""
+    nx, ny, nz = dims
+    if index is None:
+        index = torch.arange(nx * ny * nz)
+    index = torch.as_tensor(index, dtype=torch.long)
+    i = index % nx
+    j = (index // nx) % ny
+    k = index // (nx * ny)
+    o = _t(origin).reshape(3)
+    return o + (torch.stack([i, j, k], 1).to(DT) + 0.5) * voxel
+
+
+def tsdf_fuse(cams_in: Sequence, depths: Sequence[torch.Tensor], origin, voxel: float, dims, trunc: float,
+              colors: Optional[Sequence[torch.Tensor]] = None, index=None, near: float = 0.01,
+              state: Optional[dict] = None) -> dict:
+    """Fuse the views' depth maps [H, W] (and colours [3, H, W]) into the voxels
+    `index` (default all) of the volume, in view order, starting from `state`
+    (tsdf, weight, color of those voxels; default empty).  Returns the new state
+    and `amb`: voxels where an FP32 evaluation may take another branch."""
+    cams = [camera(c) for c in cams_in]
+    X = voxel_centres(origin, voxel, dims, index)
+    n = X.shape[0]
+    T = torch.zeros(n, dtype=DT) if state is None else _t(state["tsdf"]).clone()
+    Wt = torch.zeros(n, dtype=DT) if state is None else _t(state["weight"]).clone()
+    Cl = torch.zeros(n, 3, dtype=DT) if state is None else _t(state["color"]).clone()
+    amb = torch.zeros(n, dtype=torch.bool)
+    for v, c in enumerate(cams):
+        D = _t(depths[v])
+        H, W = D.shape
+        pc = _to_cam(c, X)
+        z = pc[:, 2]
+        front = z > near
+        zs = torch.where(front, z, torch.ones_like(z))
+        u = c["fx"] * pc[:, 0] / zs + c["cx"]
+        w = c["fy"] * pc[:, 1] / zs + c["cy"]
+        px, py = torch.floor(u), torch.floor(w)
+        inside = front & (px >= 0) & (py >= 0) & (px <= W - 1) & (py <= H - 1)
+        ix = px.clamp(0, W - 1).long()
+        iy = py.clamp(0, H - 1).long()
+        d = D[iy, ix]
+        sdf = d - z
+        upd = inside & (d > 0) & (sdf >= -trunc)
+        obs = torch.clamp(sdf / trunc, max=1.0)
+        T = torch.where(upd, (T * Wt + obs) / (Wt + 1), T)
+        if colors is not None:
+            col = _t(colors[v])[:, iy, ix].T
+            Cl = torch.where(upd[:, None], (Cl * Wt[:, None] + col) / (Wt[:, None] + 1), Cl)
+        Wt = torch.where(upd, Wt + 1, Wt)
+        fu, fw = u - px, w - py
+        amb |= front & (((fu < AMB_TSDF_PIX) | (fu > 1 - AMB_TSDF_PIX) | (fw < AMB_TSDF_PIX)
+                         | (fw > 1 - AMB_TSDF_PIX)) & (u > -1) & (w > -1) & (u < W + 1) & (w < H + 1))
+        amb |= inside & (d > 0) & ((sdf + trunc).abs() < AMB_TSDF_SDF)
+        amb |= (z - near).abs() < AMB_TSDF_NEAR * max(1.0, near)
+    return dict(tsdf=T, weight=Wt, color=Cl, amb=amb)
