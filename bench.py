@@ -117,6 +117,7 @@ def resolution_desc(cams) -> str:
 
 N_SPARSE = 50_000   # sparse-cloud stand-in for the depth-prior scale/shift fit
 N_PATCH = 65_536    # patch centres per view pair for the batch geometric NCC (Eq. 10)
+TSDF_REPS = 10      # timed TSDF fusions of the rendered batch
 LAMBDA_NCC = 0.2    # NCC weight at the end of the paper's schedule
 
 
@@ -464,6 +465,38 @@ def run_pgs(args):
         em += e0.elapsed_time(e1)
     e2e_vps = world * V * ke / (em / 1e3)
 
+    # TSDF fusion of the rendered batch (mesh reconstruction; not part of the training step):
+    # a 400 x 400 x 200 volume of 0.01 with truncation 0.04, fused TSDF_REPS times
+    tsdf = None
+    if not args.no_tsdf:
+        dims = (400, 400, 200)
+        nvox = dims[0] * dims[1] * dims[2]
+        vol = dict(origin=(-2.0, -2.0, -1.0), voxel=0.01, dims=dims, trunc=0.04,
+                   tsdf=torch.zeros(nvox, device=device), weight=torch.zeros(nvox, device=device),
+                   color=torch.zeros(nvox, 3, device=device))
+        with torch.cuda.stream(stream):
+            scene.tsdf_integrate(cams, images.depth, vol, rgb=images.rgb, stream=stream, packed=packed)
+        stream.synchronize()
+        n_upd = int((vol["weight"] > 0).sum())
+        tm = 0.0
+        for _ in range(TSDF_REPS):
+            with torch.cuda.stream(stream):
+                flush.fill_(1.0)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                scene.tsdf_integrate(cams, images.depth, vol, rgb=images.rgb, stream=stream, packed=packed)
+                e1.record(stream)
+            e1.synchronize()
+            tm += e0.elapsed_time(e1)
+        scene.read_status(stream)
+        t_ms = tm / TSDF_REPS
+        nbytes = 20 * nvox + 20 * n_upd + 16 * int(n_pix)
+        tsdf = dict(ms=t_ms, voxels=nvox, updated_voxels=n_upd, views=V, voxel_views_per_s=nvox * V / (t_ms / 1e3),
+                    bytes_per_launch=nbytes, achieved_gbs=nbytes / (t_ms / 1e3) / 1e9,
+                    volume="400x400x200 voxels of 0.01, truncation 0.04, rendered depth and colour of the batch")
+        del vol
+
     # roofline of the dominant kernel
     peaks = _peaks()
     dom = max(("blend_bwd", "blend_fwd", "tile_sort", "depth_sort", "project", "project_bwd", "wgrad", "bin", "loss",
@@ -525,6 +558,7 @@ def run_pgs(args):
                     e2e=dict(value=e2e_vps, unit="views/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h),
                     gpu_launches=launches_per_step * args.steps,
                     roofline=roof, stage_ms=stage_ms, cpu_baseline=cpu, clocks=clocks,
+                    tsdf=(dict(tsdf, frac_of_hbm=tsdf["achieved_gbs"] / peaks["hbm_gbs"]) if tsdf else None),
                     counts=dict(rows=int(stats.rows), gaussian_views=int(stats.gaussian_views), pairs=P,
                                 tiles=int(stats.tiles), pixels=int(stats.pixels), n_eval=n_eval, n_contrib=n_contrib),
                     wall_s=wall)
@@ -543,6 +577,7 @@ def main():
     ap.add_argument("--workload", default="batch8_1600")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-tsdf", action="store_true", help="skip the TSDF fusion measurement")
     ap.add_argument("--no-tune", action="store_true", help="skip the launch-shape autotuner (16x16 tiles, batch 256)")
     ap.add_argument("--decode", default="bf16", choices=("bf16", "fp32"), help="decoder precision of the batched form")
     ap.add_argument("--cap-pairs", type=int, default=None, help="pair capacity (default 2^29)")

@@ -245,7 +245,8 @@ enum pgs_stage {
   PGS_STAGE_WGRAD = 8,        /* decoder weight-gradient reduction */
   PGS_STAGE_PRIOR = 9,        /* enhanced depth prior (pgs_filter_depth_prior) */
   PGS_STAGE_NCC = 10,         /* batch geometric NCC loss (pgs_ncc_loss_grad) */
-  PGS_N_STAGES = 11
+  PGS_STAGE_TSDF = 11,        /* TSDF fusion (pgs_tsdf_integrate) */
+  PGS_N_STAGES = 12
 };
 pgs_status pgs_set_profiling(pgs_scene* s, int enable);
 pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);
@@ -343,6 +344,32 @@ typedef struct pgs_ncc_params {
 pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, const pgs_image_ptrs* img,
                              const uint32_t* d_centers, int64_t n_per_pair, const pgs_ncc_params* np,
                              float* d_ncc, float* d_loss, const pgs_image_grad_ptrs* grad, cudaStream_t stream);
+
+/* Projective TSDF fusion of rendered depth and colour into a voxel volume
+ * (supplementary, mesh reconstruction: voxel 0.01, truncation 0.04 for the
+ * aerial scenes; the paper cites Zeng et al.'s TSDF fusion).  For each voxel
+ * (i, j, k), centred at origin + (i + 1/2, j + 1/2, k + 1/2) * voxel, and each
+ * view in batch order: camera depth z of the centre > near plane (the scene's
+ * render parameters); its nearest pixel (floor of the projection, pixel
+ * centres at +1/2) inside the frame with depth D > 0; sdf = D - z >= -trunc;
+ * then tsdf <- (tsdf W + min(1, sdf / trunc)) / (W + 1), colour likewise with
+ * the pixel's colour, W <- W + 1.  Voxels no view updates are not written.
+ * d_depth: per-pixel z-depth in the image arena layout (D_hat of a render,
+ * <= 0 = none); d_rgb: [3 x pix] colour (may be NULL, then d_color must be
+ * NULL too).  Volume state (device, caller-owned, x fastest: linear index
+ * (k ny + j) nx + i): d_tsdf and d_weight float[n], d_color float[n][3] or
+ * NULL; initialise weight to 0 and tsdf / colour to finite values (0) before
+ * the first call; later calls keep fusing.  Errors: PGS_ERR_INVALID_ARG for
+ * null pointers, dims < 1, voxel <= 0 or trunc <= 0. */
+typedef struct pgs_tsdf_volume {
+  float origin[3];              /* world position of the corner of voxel (0, 0, 0) */
+  float voxel;                  /* voxel edge length */
+  int32_t dims[3];              /* nx, ny, nz */
+  float trunc;                  /* truncation band of the signed distance */
+} pgs_tsdf_volume;
+pgs_status pgs_tsdf_integrate(pgs_scene* s, const pgs_camera* cams, int n_views, const float* d_depth,
+                              const float* d_rgb, const pgs_tsdf_volume* vol, float* d_tsdf, float* d_weight,
+                              float* d_color, cudaStream_t stream);
 
 /* The scene's current render parameters (as created, or as the autotuner set them). */
 pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out);

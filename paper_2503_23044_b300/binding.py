@@ -111,6 +111,10 @@ class NccParams(C.Structure):
     _fields_ = [("lambda_ncc", C.c_float), ("eps", C.c_float), ("geometric", C.c_int32)]
 
 
+class TsdfVolume(C.Structure):
+    _fields_ = [("origin", C.c_float * 3), ("voxel", C.c_float), ("dims", C.c_int32 * 3), ("trunc", C.c_float)]
+
+
 class TuneEntry(C.Structure):
     _fields_ = [("tile_w", C.c_int32), ("tile_h", C.c_int32), ("blend_batch", C.c_int32), ("ms", C.c_float)]
 
@@ -120,9 +124,9 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
-                "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad")
+                "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad", "pgs_tsdf_integrate")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad",
-          "prior", "ncc")
+          "prior", "ncc", "tsdf")
 
 
 def _declare(L: C.CDLL) -> None:
@@ -163,6 +167,7 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_filter_depth_prior.argtypes = [vp, P(Camera), i32, vp, vp, i64, P(PriorParams), vp, vp, vp, vp, vp]
     L.pgs_ncc_loss_grad.argtypes = [vp, P(Camera), i32, P(ImagePtrs), vp, i64, P(NccParams), vp, vp,
                                     P(ImageGradPtrs), vp]
+    L.pgs_tsdf_integrate.argtypes = [vp, P(Camera), i32, vp, vp, P(TsdfVolume), vp, vp, vp, vp]
 
 
 def check(status: int) -> None:
@@ -414,6 +419,18 @@ class Scene:
                                       _ptr(centers) if centers.numel() else None, n_per, C.byref(npar),
                                       _ptr(ncc_out), _ptr(loss), C.byref(grads.ptrs()), _stream(stream)))
         return dict(ncc=ncc_out[:n_pairs * n_per].view(n_pairs, n_per), loss=loss)
+
+    def tsdf_integrate(self, cams, depth: torch.Tensor, volume: dict, rgb: Optional[torch.Tensor] = None,
+                       stream=None, packed=None) -> dict:
+        """TSDF fusion (pgs_tsdf_integrate) of depth (and colour) maps in the arena layout into
+        volume = dict(origin, voxel, dims, trunc, tsdf, weight[, color]) (state tensors updated in place)."""
+        cc = packed if packed is not None else pack_cameras(cams)
+        vol = TsdfVolume((C.c_float * 3)(*volume["origin"]), volume["voxel"], (C.c_int32 * 3)(*volume["dims"]),
+                         volume["trunc"])
+        color = volume.get("color") if rgb is not None else None
+        check(lib().pgs_tsdf_integrate(self.handle, cc, len(cams), _ptr(depth), _ptr(rgb), C.byref(vol),
+                                       _ptr(volume["tsdf"]), _ptr(volume["weight"]), _ptr(color), _stream(stream)))
+        return volume
 
     def params(self) -> dict:
         p = RenderParams()

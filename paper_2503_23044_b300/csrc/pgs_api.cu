@@ -614,6 +614,34 @@ pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, 
   return PGS_OK;
 }
 
+pgs_status pgs_tsdf_integrate(pgs_scene* s, const pgs_camera* cams, int n_views, const float* d_depth,
+                              const float* d_rgb, const pgs_tsdf_volume* vol, float* d_tsdf, float* d_weight,
+                              float* d_color, cudaStream_t st) {
+  if (!s || !vol || !d_depth || !d_tsdf || !d_weight) return fail(PGS_ERR_INVALID_ARG, "null argument");
+  if ((d_rgb == nullptr) != (d_color == nullptr)) return fail(PGS_ERR_INVALID_ARG, "colour in and out go together");
+  if (vol->dims[0] < 1 || vol->dims[1] < 1 || vol->dims[2] < 1)
+    return fail(PGS_ERR_INVALID_ARG, "dims %d x %d x %d", vol->dims[0], vol->dims[1], vol->dims[2]);
+  if (!(vol->voxel > 0.f) || !(vol->trunc > 0.f) || !std::isfinite(vol->origin[0]) ||
+      !std::isfinite(vol->origin[1]) || !std::isfinite(vol->origin[2]))
+    return fail(PGS_ERR_INVALID_ARG, "voxel, trunc or origin");
+  BatchDev b;
+  pgs_status r = build_batch(s, cams, n_views, b);
+  if (r) return r;
+  TsdfArgs a;
+  for (int k = 0; k < 3; ++k) {
+    a.origin[k] = vol->origin[k];
+    a.dims[k] = vol->dims[k];
+  }
+  a.voxel = vol->voxel;
+  a.trunc = vol->trunc;
+  prof_mark(s, PGS_STAGE_TSDF, 0, st);
+  launch_tsdf(b, a, d_depth, d_rgb, d_tsdf, d_weight, d_color, s->num_sms, st);
+  s->launches += 1;
+  prof_mark(s, PGS_STAGE_TSDF, 1, st);
+  PGS_CUDA(cudaGetLastError());
+  return PGS_OK;
+}
+
 pgs_status pgs_scene_get_params(const pgs_scene* s, pgs_render_params* out) {
   if (!s || !out) return fail(PGS_ERR_INVALID_ARG, "null argument");
   *out = s->d.params;

@@ -107,6 +107,13 @@ void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, lo
                 const float* rgb, const float* depth, const float* normal, float* ncc, float* loss, float* g_rgb,
                 float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms, cudaStream_t st);
 size_t ncc_scratch_bytes();
+// TSDF fusion: the volume and the truncation band
+struct TsdfArgs {
+  float origin[3], voxel, trunc;
+  int dims[3];
+};
+void launch_tsdf(const BatchDev& b, const TsdfArgs& a, const float* depth, const float* rgb, float* tsdf,
+                 float* weight, float* color, int num_sms, cudaStream_t st);
 void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp, const float* pts, long long n_pts,
                          float* partials, float* means, float* scale_shift, float* prior_out, float* mask_out,
                          float* err_out, int num_sms, cudaStream_t st);

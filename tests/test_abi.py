@@ -44,6 +44,9 @@ def test_struct_sizes_match_header_layout():
     assert ctypes.sizeof(B.ImagePtrs) == 8 * 8
     assert ctypes.sizeof(B.ParamGradPtrs) == 13 * 8
     assert ctypes.sizeof(B.Stats) == 7 * 8
+    assert ctypes.sizeof(B.PriorParams) == 2 * 4
+    assert ctypes.sizeof(B.NccParams) == 3 * 4
+    assert ctypes.sizeof(B.TsdfVolume) == 8 * 4
 
 
 def test_default_params_and_argument_errors_without_gpu():
