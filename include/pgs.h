@@ -360,7 +360,7 @@ pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, 
  * (k ny + j) nx + i): d_tsdf and d_weight float[n], d_color float[n][3] or
  * NULL; initialise weight to 0 and tsdf / colour to finite values (0) before
  * the first call; later calls keep fusing.  Errors: PGS_ERR_INVALID_ARG for
- * null pointers, dims < 1, voxel <= 0 or trunc <= 0. */
+ * null pointers, dims < 1 or more than 2^34 voxels, voxel <= 0 or trunc <= 0. */
 typedef struct pgs_tsdf_volume {
   float origin[3];              /* world position of the corner of voxel (0, 0, 0) */
   float voxel;                  /* voxel edge length */

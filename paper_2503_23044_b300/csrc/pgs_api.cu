@@ -619,7 +619,8 @@ pgs_status pgs_tsdf_integrate(pgs_scene* s, const pgs_camera* cams, int n_views,
                               float* d_color, cudaStream_t st) {
   if (!s || !vol || !d_depth || !d_tsdf || !d_weight) return fail(PGS_ERR_INVALID_ARG, "null argument");
   if ((d_rgb == nullptr) != (d_color == nullptr)) return fail(PGS_ERR_INVALID_ARG, "colour in and out go together");
-  if (vol->dims[0] < 1 || vol->dims[1] < 1 || vol->dims[2] < 1)
+  if (vol->dims[0] < 1 || vol->dims[1] < 1 || vol->dims[2] < 1 ||
+      (long long)vol->dims[0] * vol->dims[1] * vol->dims[2] > (1ll << 34))
     return fail(PGS_ERR_INVALID_ARG, "dims %d x %d x %d", vol->dims[0], vol->dims[1], vol->dims[2]);
   if (!(vol->voxel > 0.f) || !(vol->trunc > 0.f) || !std::isfinite(vol->origin[0]) ||
       !std::isfinite(vol->origin[1]) || !std::isfinite(vol->origin[2]))
