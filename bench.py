@@ -252,6 +252,21 @@ def run_reference(args):
     return 0
 
 
+# ------------------------------------------------------------------ ranks
+def max_over_ranks(ms: float, dist, device) -> float:
+    """The slowest rank's time for a region every rank brackets with barriers (no-op on one rank)."""
+    if dist is None:
+        return ms
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, n_ranks: int, ms: float) -> float:
+    """Whole-job throughput: every rank processes its own batch (weak scaling), the job takes the slowest time."""
+    return n_ranks * units_per_rank / (ms / 1e3)
+
+
 # ------------------------------------------------------------------ GPU arm
 def arena_slice(B, img, grads, v0: int, v1: int):
     """Images and image gradients of views v0 .. v1 - 1 as views of a batch arena."""
@@ -380,13 +395,9 @@ def run_pgs(args):
     if dist is not None:
         dist.barrier()
     scene.read_status(stream)
-    tot_ms = float(sum(step_ms))
-    if dist is not None:
-        tt = torch.tensor([tot_ms], device=device)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        tot_ms = float(tt.item())
+    tot_ms = max_over_ranks(float(sum(step_ms)), dist, device)
     ms_per_step = tot_ms / args.steps
-    value = world * V * args.steps / (tot_ms / 1e3)
+    value = job_rate(V * args.steps, world, tot_ms)
     stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
     stats = scene.stats(stream)
     scene.set_profiling(False)
@@ -441,7 +452,7 @@ def run_pgs(args):
             e1.synchronize()
             pm += e0.elapsed_time(e1)
         pscene.read_status(stream)
-        plain_vps = V * ks / (pm / 1e3)
+        plain_vps = job_rate(V * ks, world, max_over_ranks(pm, dist, device))
         pscene.close()
 
     # end to end through the public API: every step's inputs (target colour, pseudo depth)
@@ -477,6 +488,8 @@ def run_pgs(args):
     with torch.cuda.stream(stream):
         runs[1]()                                   # warm the second graph
     stream.synchronize()
+    if dist is not None:
+        dist.barrier()
     e0 = torch.cuda.Event(enable_timing=True)
     e1 = torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -500,8 +513,8 @@ def run_pgs(args):
             host_loss[4:].copy_(ncc_loss, non_blocking=True)
     e1.record(stream)
     e1.synchronize()
-    em = e0.elapsed_time(e1)
-    e2e_vps = world * V * ke / (em / 1e3)
+    em = max_over_ranks(e0.elapsed_time(e1), dist, device)
+    e2e_vps = job_rate(V * ke, world, em)
 
     # TSDF fusion of the rendered batch (mesh reconstruction; not part of the training step):
     # a 400 x 400 x 200 volume of 0.01 with truncation 0.04, fused TSDF_REPS times
