@@ -475,7 +475,7 @@ def loss_and_image_grads(maps: Sequence[dict], targets: Sequence[dict], cams: Se
     L = batch_loss(leaves, targets, cams, lp)
     L["total"].backward()
     grads = [{k: lv[k].grad.detach().clone() for k in lv} for lv in leaves]
-    return float(L["total"]), grads, L
+    return float(L["total"].detach()), grads, L
 
 
 def loss_ambiguity(maps: Sequence[dict], targets: Sequence[dict], tol: float = 1e-5):
