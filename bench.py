@@ -118,6 +118,10 @@ def resolution_desc(cams) -> str:
 N_SPARSE = 50_000   # sparse-cloud stand-in for the depth-prior scale/shift fit
 N_PATCH = 65_536    # patch centres per view pair for the batch geometric NCC (Eq. 10)
 TSDF_REPS = 10      # timed TSDF fusions of the rendered batch
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of the kernel on
+# that workload; drop an entry whenever its kernel changes
+MEASURED_TRAFFIC = {("batch8_1600", "blend_bwd"): 914.9e6 + 86.3e6,
+                    ("batch8_1600", "blend_fwd"): 137.0e6 + 491.3e6}
 LAMBDA_NCC = 0.2    # NCC weight at the end of the paper's schedule
 
 
@@ -561,7 +565,7 @@ def run_pgs(args):
              (FWD_FLOPS_EVAL * n_eval + FWD_FLOPS_CONTRIB * n_contrib)
         ach = fl / (stage_ms[dom] / 1e3) / 1e12
         roof = dict(bound="alu", kernel=f"k_{dom}", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                    traffic=None, flops_per_launch=fl, peak_src=f"{sm_count} SMs x 128 FP32 lanes x 2 x "
+                    traffic=MEASURED_TRAFFIC.get((args.workload, dom)), flops_per_launch=fl, peak_src=f"{sm_count} SMs x 128 FP32 lanes x 2 x "
                     f"{peaks['sm_max_mhz']:.0f} MHz")
     else:
         nb = {"tile_sort": 2 * 16 * P * math.ceil(max(1, math.log2(max(2, stats.tiles))) / 8) + 4 * P,
