@@ -64,9 +64,13 @@ __device__ __forceinline__ void stage_record(BlendSmem<NB>& s, int slot, const f
   s.n[slot] = r.n;
 }
 
-// power of the Gaussian at the pixel, with the exact operation order shared by both passes
+// power of the Gaussian at the pixel, with the exact operation order shared by both passes,
+// from the products dx^2, dx dy, dy^2 (the backward reuses them for the conic sums)
+__device__ __forceinline__ float eval_power_xy(const float4 q, float xx, float xy, float yy) {
+  return __fmaf_rn(q.x, xx, __fmaf_rn(q.z, yy, __fmul_rn(q.y, xy)));
+}
 __device__ __forceinline__ float eval_power(const float4 q, float dx, float dy) {
-  return __fmaf_rn(q.x, __fmul_rn(dx, dx), __fmaf_rn(q.z, __fmul_rn(dy, dy), __fmul_rn(q.y, __fmul_rn(dx, dy))));
+  return eval_power_xy(q, __fmul_rn(dx, dx), __fmul_rn(dx, dy), __fmul_rn(dy, dy));
 }
 
 struct PixF {            // forward state of one pixel
@@ -269,7 +273,8 @@ __device__ __forceinline__ void bwd_pair(const RecF& r, float2 mt, uint32_t j, b
                                          const float4 g1, const float2 f, float& T, float& GS,
                                          float acc[kGradFields], float a_max) {
   const float dx = __fsub_rn(f.x, mt.x), dy = __fsub_rn(f.y, mt.y);
-  const float power = eval_power(r.q, dx, dy);
+  const float xx = __fmul_rn(dx, dx), xy = __fmul_rn(dx, dy), yy = __fmul_rn(dy, dy);
+  const float power = eval_power_xy(r.q, xx, xy, yy);
   const bool take = act && j < __float_as_uint(g1.w) && !(power > 0.f) && power >= r.n.w;
   const float a_raw = __fmul_rn(r.q.w, ex2_approx(power));
   const float alpha = fminf(a_max, a_raw);
@@ -289,9 +294,9 @@ __device__ __forceinline__ void bwd_pair(const RecF& r, float2 mt, uint32_t j, b
   const float G = (take && !(a_raw > a_max)) ? dLda * a_raw : 0.f;
   acc[0] = fmaf(G, dx, acc[0]);
   acc[1] = fmaf(G, dy, acc[1]);
-  acc[2] = fmaf(G, dx * dx, acc[2]);
-  acc[3] = fmaf(G, dx * dy, acc[3]);
-  acc[4] = fmaf(G, dy * dy, acc[4]);
+  acc[2] = fmaf(G, xx, acc[2]);
+  acc[3] = fmaf(G, xy, acc[3]);
+  acc[4] = fmaf(G, yy, acc[4]);
   acc[5] += G;
 }
 
