@@ -468,7 +468,7 @@ def run_pgs(args):
     host_loss = torch.zeros(6).pin_memory()
     h2d = sum(x.numel() * x.element_size() for x in host_t)
     d2h = host_loss.numel() * 4
-    ke = max(2, min(args.steps, 20))
+    ke = max(2, min(args.steps, 50))
     sets = [(targets, pseudo),
             (B.Targets(torch.empty_like(targets.rgb), targets.prior, targets.mask), torch.empty_like(pseudo))]
     runs = [run]
