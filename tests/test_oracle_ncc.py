@@ -194,6 +194,9 @@ def test_gradients_match_finite_differences():
         fd = (L(lambda mp: plus(mp, 1.0)) - L(lambda mp: plus(mp, -1.0))) / (2 * h)
         an = float(g[1][key][idx])
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)) + 1e-9, (key, idx, fd, an)
+    # NCC ignores a brightness offset of the reference patch, so each patch's colour gradient sums to zero
+    for ch in range(3):
+        assert abs(float(g[1]["rgb"][ch].sum())) <= 1e-12 * float(g[1]["rgb"][ch].abs().sum())
     # the literal stop-gradient: the same colour gradient, no geometric one
     lit = O.ncc_loss(cams, maps, [centers.tolist()], geo=False)["grads"]
     assert float(lit[1]["depth"].abs().max()) == 0.0 and float(lit[1]["normal"].abs().max()) == 0.0
