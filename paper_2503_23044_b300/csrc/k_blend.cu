@@ -242,15 +242,17 @@ __device__ __forceinline__ void finish_grads(const float* a, float4 q, float out
 }
 
 // Backward, record-parallel within the tile: one warp per tile.  The tile's
-// list is taken back to front in chunks of up to 32 records, lane l holding
-// record cbase + l.  The pixels that still have contributors at or below the
-// chunk's top (last > cbase) stream through the lanes from the top lane down
-// to lane 0, one lane per step, so each pixel meets the chunk's records in
-// descending order as the reverse pass requires.  A pixel's running state
-// (T, GS) moves down one lane per step by shuffle and is parked in shared
-// memory between chunks.  Each lane sums its own record's per-pixel terms in
-// registers (no cross-lane reduction) and adds the record's gradient to
-// global memory once per (record, tile).
+// list is taken back to front in chunks of up to 32 records held by each of two
+// 16-lane groups (two records per lane; chunks of up to 16, one record per lane,
+// in 2 or 4 groups).  The pixels that still have contributors at or below the
+// chunk's top (last > cbase) are split between the groups, and within a group
+// stream through the lanes from the top lane down to lane 0, one lane per step,
+// so each pixel meets the chunk's records in descending order as the reverse
+// pass requires.  A pixel's running state (T, GS) moves down one lane per step
+// by shuffle and is parked in shared memory between chunks.  Each lane sums its
+// own records' per-pixel terms in registers (no reduction per pixel), the groups'
+// sums are added once per chunk, and each record's gradient goes to global
+// memory once per (record, tile).
 //   acc[0..5]  = sum G dx, G dy, G dx^2, G dx dy, G dy^2, G   (G = dL/dalpha * alpha_raw)
 //   acc[6..12] = sum w gC (3), w gD, w gN (3)
 // dL/dalpha_i = T_i (g . f_i) - (g . S_i) / (1 - alpha_i), with g . S_i carried as one scalar GS.
@@ -360,17 +362,23 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
   end = min(__reduce_max_sync(FULL, end), rg.y);   // a stale `last` never walks past the tile's list
   for (uint32_t cend = end; cend > rg.x;) {
     const uint32_t avail = cend - rg.x;
-    if (avail > 32) {
-      // Dual chunk of 33..64 records: lane l holds records B = cbase + l + min(l, n2)
-      // and, for l < n2, A = B + 1; a pixel meets A then B in each lane, so
-      // the per-step overhead (pixel loads, shuffles, state) serves two pairs.
-      const int n_rec = (int)min(avail, 64u);
+    if (avail > 16) {
+      // Chunk of 17..32 records in two lane groups of 16: lane li = lane % 16 of each
+      // group holds records B = cbase + li + min(li, n2) and, for li < n2, A = B + 1;
+      // each group runs its own 16-lane pipeline over half of the live pixels (a pixel
+      // meets A then B in each lane, from lane 15 down to lane 0), so the pipeline fill
+      // is 15 steps and a pixel's top chunk holds at most 32 records; the two groups'
+      // sums are added before the atomics.
+      const int n_rec = (int)min(avail, 32u);
       const uint32_t cbase = cend - n_rec;
-      const int n2 = n_rec - 32;
+      const int n2 = n_rec - 16;
+      const int li = lane & 15, grp = lane >> 4;
       __syncwarp();
       const int n_live = build_live(tab, cbase, lane);
-      const uint32_t jB = cbase + lane + min(lane, n2), jA = jB + 1;
-      const bool hasA = lane < n2;
+      const int seg = (n_live + 1) >> 1;
+      const int seg_lo = grp * seg, seg_hi = min(n_live, seg_lo + seg);
+      const uint32_t jB = cbase + li + min(li, n2), jA = jB + 1;
+      const bool hasA = li < n2;
       const uint32_t gB = pair_g[jB], gA = hasA ? pair_g[jA] : 0u;
       const RecF rB = load_record(rec, gB, a_min);
       RecF rA{};
@@ -381,37 +389,45 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
       for (int f = 0; f < kGradFields; ++f) accA[f] = accB[f] = 0.f;
       __syncwarp();
       float T = 0.f, GS = 0.f;
-      const int nsteps = n_live + 31;
+      const int nsteps = seg + 15;
 #pragma unroll 2
       for (int s = 0; s < nsteps; ++s) {
-        const int pi = s - 31 + lane;
-        const bool act = (unsigned)pi < (unsigned)n_live;
+        const int q = s - 15 + li;             // position in this group's slice
+        const int pi = seg_lo + q;
+        const bool act = q >= 0 && pi < seg_hi;
         const int pix = tab.live[act ? pi : 0];
         const float4 g1 = tab.g1[pix];
         const float2 f = tab.f[pix];
         const float4 g0 = tab.g0[pix];
-        T = __shfl_down_sync(FULL, T, 1);
-        GS = __shfl_down_sync(FULL, GS, 1);
-        if (lane == 31) {
+        T = __shfl_down_sync(FULL, T, 1, 16);
+        GS = __shfl_down_sync(FULL, GS, 1, 16);
+        if (li == 15) {
           const float2 t = tab.st[pix];
           T = t.x;
           GS = t.y;
         }
         bwd_pair(rA, mtA, jA, act && hasA, g0, g1, f, T, GS, accA, a_max);
         bwd_pair(rB, mtB, jB, act, g0, g1, f, T, GS, accB, a_max);
-        if (act && lane == 0) tab.st[pix] = make_float2(T, GS);
+        if (act && li == 0) tab.st[pix] = make_float2(T, GS);
       }
-      flush_record(accB, rB.q, gB, grad);
-      if (hasA) flush_record(accA, rA.q, gA, grad);
+#pragma unroll
+      for (int f = 0; f < kGradFields; ++f) {
+        accA[f] += __shfl_xor_sync(FULL, accA[f], 16);
+        accB[f] += __shfl_xor_sync(FULL, accB[f], 16);
+      }
+      if (grp == 0) {
+        flush_record(accB, rB.q, gB, grad);
+        if (hasA) flush_record(accA, rA.q, gA, grad);
+      }
       cend = cbase;
       continue;
     }
-    // Single chunk of up to 32 records (the tile's last): lane l holds record
-    // cbase + l.  A short chunk is replicated into 2 or 4 lane groups that take
+    // Single chunk of up to 16 records (the tile's last): lane l of each group holds
+    // record cbase + l; the chunk is replicated into 2 or 4 lane groups that take
     // separate slices of the live pixels; their sums are combined before the atomics.
     const uint32_t cbase = rg.x;
     const int n_rec = (int)avail;
-    const int gsz = n_rec <= 8 ? 8 : (n_rec <= 16 ? 16 : 32);
+    const int gsz = n_rec <= 8 ? 8 : 16;
     const int lig = lane & (gsz - 1), grp = lane / gsz;
     const int top = n_rec - 1;                 // lane (in its group) of the chunk's last record
     __syncwarp();
