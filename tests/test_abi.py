@@ -82,3 +82,20 @@ def test_stage_names_match_header_enum():
     assert len(B.STAGES) == n == len(stages)
     for i, name in enumerate(B.STAGES):
         assert stages[name] == i, name
+
+
+def test_new_entry_points_reject_null_arguments_without_gpu():
+    """The depth-prior, NCC and TSDF calls validate their arguments before any
+    device work: a null scene or parameter block is an argument error."""
+    L = _lib()
+    pp = B.PriorParams(1.0, 2)
+    assert L.pgs_filter_depth_prior(None, None, 2, None, None, 0, ctypes.byref(pp), None, None, None, None,
+                                    None) == B.PGS_ERR_INVALID_ARG
+    npar = B.NccParams(0.2, 1e-6, 1)
+    img, grad = B.ImagePtrs(), B.ImageGradPtrs()
+    assert L.pgs_ncc_loss_grad(None, None, 2, ctypes.byref(img), None, 16, ctypes.byref(npar), None, None,
+                               ctypes.byref(grad), None) == B.PGS_ERR_INVALID_ARG
+    vol = B.TsdfVolume((ctypes.c_float * 3)(0, 0, 0), 0.01, (ctypes.c_int32 * 3)(4, 4, 4), 0.04)
+    assert L.pgs_tsdf_integrate(None, None, 1, None, None, ctypes.byref(vol), None, None, None,
+                                None) == B.PGS_ERR_INVALID_ARG
+    assert b"null" in L.pgs_last_error()
