@@ -91,6 +91,29 @@ __device__ __forceinline__ void range_of_block(long long n, long long& s, long l
 constexpr int kCountUnroll = 4;  // pixels per thread per iteration, loads first
 constexpr int kGradUnroll = 2;
 
+// A thread's pixels run through the views in order, so it counts in registers for
+// its current view and adds to the block's shared counters only when the view
+// changes (integer sums: the result does not depend on the order).
+struct ViewCounts {
+  int v = -1;
+  uint32_t c0 = 0, c1 = 0;
+  __device__ __forceinline__ void flush(uint32_t (*s_cnt)[2]) {
+    if (v >= 0) {
+      if (c0) atomicAdd(&s_cnt[v][0], c0);
+      if (c1) atomicAdd(&s_cnt[v][1], c1);
+    }
+    c0 = c1 = 0;
+  }
+  __device__ __forceinline__ void add(uint32_t (*s_cnt)[2], int pv, bool m, bool nv) {
+    if (pv != v) {
+      flush(s_cnt);
+      v = pv;
+    }
+    c0 += m ? 1u : 0u;
+    c1 += nv ? 1u : 0u;
+  }
+};
+
 __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ BatchDev b, pgs_image_ptrs img,
                                                      pgs_target_ptrs tgt, uint32_t* __restrict__ counts) {
   __shared__ uint32_t s_cnt[kMaxViews][2];
@@ -102,6 +125,7 @@ __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ Bat
   long long s, e;
   range_of_block(b.total_pixels, s, e);
   int vh = s < e ? view_of_pixel(b, s) : 0;
+  ViewCounts vc;
   for (long long p0 = s + threadIdx.x; p0 < e; p0 += kCountUnroll * (long long)blockDim.x) {
     PixIn I[kCountUnroll];
 #pragma unroll
@@ -114,10 +138,10 @@ __global__ void __launch_bounds__(256) k_loss_counts(const __grid_constant__ Bat
       const long long p = p0 + u * (long long)blockDim.x;
       if (p >= e) break;
       float nd[3], nn;
-      if (I[u].mask > 0.f) atomicAdd(&s_cnt[I[u].c.v][0], 1u);
-      if (normal_valid(b, I[u], nd, nn)) atomicAdd(&s_cnt[I[u].c.v][1], 1u);
+      vc.add(s_cnt, I[u].c.v, I[u].mask > 0.f, normal_valid(b, I[u], nd, nn));
     }
   }
+  vc.flush(s_cnt);
   __syncthreads();
   for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x)
     if ((&s_cnt[0][0])[i]) atomicAdd(counts + i, (&s_cnt[0][0])[i]);
@@ -261,6 +285,7 @@ __global__ void __launch_bounds__(256) k_loss_counts4(const __grid_constant__ Ba
   long long s, e;
   range_of_block(b.total_pixels / 4, s, e);
   int vh = s < e ? view_of_pixel(b, 4 * s) : 0;
+  ViewCounts vc;
   for (long long q0 = s + threadIdx.x; q0 < e; q0 += 2 * (long long)blockDim.x) {
     PixIn I[2][4];
 #pragma unroll
@@ -274,11 +299,11 @@ __global__ void __launch_bounds__(256) k_loss_counts4(const __grid_constant__ Ba
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         float nd[3], nn;
-        if (I[u][i].mask > 0.f) atomicAdd(&s_cnt[I[u][i].c.v][0], 1u);
-        if (normal_valid(b, I[u][i], nd, nn)) atomicAdd(&s_cnt[I[u][i].c.v][1], 1u);
+        vc.add(s_cnt, I[u][i].c.v, I[u][i].mask > 0.f, normal_valid(b, I[u][i], nd, nn));
       }
     }
   }
+  vc.flush(s_cnt);
   __syncthreads();
   for (int i = threadIdx.x; i < kMaxViews * 2; i += blockDim.x)
     if ((&s_cnt[0][0])[i]) atomicAdd(counts + i, (&s_cnt[0][0])[i]);

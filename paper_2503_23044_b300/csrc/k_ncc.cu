@@ -262,7 +262,7 @@ __global__ void __launch_bounds__(256, 3) k_ncc_patch(const __grid_constant__ Ba
   long long j = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5);
   float flag = j < n ? ncc[j] : kNccInvalid;
   unsigned cidx = flag != kNccInvalid ? __ldg(centers + j) : 0u;
-  Centre C;
+  Centre C{};
   float dn = 0.f, nn[3] = {0.f, 0.f, 0.f};
   if (flag != kNccInvalid) {
     const ViewDev& vr = b.v[2 * (int)(j / n_per) + 1];
@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256, 3) k_ncc_patch(const __grid_constant__ Ba
       if (lane == 0) ncc[j] = val;
     }
     // the next patch's centre depth and normal
-    Centre Cn;
+    Centre Cn = C;                                            // overwritten below for a used patch
     float dn_n = 0.f, nn_n[3] = {0.f, 0.f, 0.f};
     if (flag_n != kNccInvalid) {
       const ViewDev& vrn = b.v[2 * (int)(jn / n_per) + 1];
