@@ -418,18 +418,17 @@ __global__ void __launch_bounds__(256) k_ncc_final(const float* __restrict__ ncc
   }
 }
 
-void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
-                const float* rgb, const float* depth, const float* normal, float* ncc, float* loss, float* g_rgb,
-                float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms, cudaStream_t st) {
+cudaError_t launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
+                       const float* rgb, const float* depth, const float* normal, float* ncc, float* loss,
+                       float* g_rgb, float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms,
+                       cudaStream_t st) {
   int* counts = reinterpret_cast<int*>(scratch);
   float* partial = reinterpret_cast<float*>(counts + kNccDone + 1);
   PairGeo* geo = reinterpret_cast<PairGeo*>(partial + kMaxViews / 2 * kNccChunks);
-  cudaMemsetAsync(counts, 0, sizeof(int) * (kNccDone + 1), st);
+  cudaError_t e = cudaMemsetAsync(counts, 0, sizeof(int) * (kNccDone + 1), st);
+  if (e != cudaSuccess) return e;
   const long long n = n_per * n_pairs;
-  if (n_pairs == 0 || n == 0) {
-    cudaMemsetAsync(loss, 0, 2 * sizeof(float), st);
-    return;
-  }
+  if (n_pairs == 0 || n == 0) return cudaMemsetAsync(loss, 0, 2 * sizeof(float), st);
   const long long n_pix = b.v[2 * n_pairs - 1].pix_off + (long long)b.v[2 * n_pairs - 1].W * b.v[2 * n_pairs - 1].H;
   bool quad = (reinterpret_cast<uintptr_t>(rgb) & 15) == 0 && (reinterpret_cast<uintptr_t>(luma) & 15) == 0;
   for (int v = 0; v < 2 * n_pairs; ++v)
@@ -442,6 +441,7 @@ void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, lo
   k_ncc_patch<<<(unsigned)blk2, 256, 0, st>>>(b, a, geo, centers, n_per, n_pairs, luma, depth, normal, counts, ncc,
                                               g_rgb, g_depth, g_normal);
   k_ncc_final<<<dim3(kNccChunks, n_pairs), 256, 0, st>>>(ncc, n_per, n_pairs, counts, partial, a.lambda, loss);
+  return cudaGetLastError();
 }
 
 size_t ncc_scratch_bytes() {

@@ -606,8 +606,8 @@ pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, 
   a.eps = np->eps;
   a.geometric = np->geometric ? 1 : 0;
   prof_mark(s, PGS_STAGE_NCC, 0, st);
-  launch_ncc(b, a, d_centers, (long long)n_per_pair, n_pairs, img->rgb, img->depth, img->normal, d_ncc, d_loss,
-             grad->rgb, grad->depth, grad->normal, s->ncc_scratch, s->ncc_luma, s->num_sms, st);
+  PGS_CUDA(launch_ncc(b, a, d_centers, (long long)n_per_pair, n_pairs, img->rgb, img->depth, img->normal, d_ncc,
+                      d_loss, grad->rgb, grad->depth, grad->normal, s->ncc_scratch, s->ncc_luma, s->num_sms, st));
   s->launches += (n_pairs > 0 && n_per_pair > 0) ? kNccLaunches : 0;
   prof_mark(s, PGS_STAGE_NCC, 1, st);
   PGS_CUDA(cudaGetLastError());

@@ -103,9 +103,10 @@ __host__ __device__ __forceinline__ size_t sc_at(long long r, int f, int width) 
 __host__ __device__ __forceinline__ long long sc_rows(long long cap) { return (cap + kScBlock - 1) / kScBlock * kScBlock; }
 
 // k_prior.cu
-void launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
-                const float* rgb, const float* depth, const float* normal, float* ncc, float* loss, float* g_rgb,
-                float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms, cudaStream_t st);
+cudaError_t launch_ncc(const BatchDev& b, const NccArgs& a, const unsigned* centers, long long n_per, int n_pairs,
+                       const float* rgb, const float* depth, const float* normal, float* ncc, float* loss,
+                       float* g_rgb, float* g_depth, float* g_normal, void* scratch, float* luma, int num_sms,
+                       cudaStream_t st);
 size_t ncc_scratch_bytes();
 // TSDF fusion: the volume and the truncation band
 struct TsdfArgs {
