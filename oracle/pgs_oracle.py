@@ -21,6 +21,15 @@ tiling, blocking or fusion:
    normal-depth consistency term.
 6. Gradients: reverse-mode differentiation of steps 2-5 by torch.autograd
    in FP64 (the exact derivative of this definition, not a hand derivation).
+7. The enhanced depth prior of Step 2 (Sec. 3.4): least-squares scale and
+   shift of a pseudo depth to sparse points, the round-trip re-projection
+   error through the nearest batch views and the tau_d filter.
+8. The batch geometric NCC of Step 3 (Eq. 10): view pairs, 7 x 7 patches
+   warped by the plane homography of the rendered depth and normal, 1 - NCC,
+   with the stop-gradient on the partner (autograd, as in 6).
+9. The projective TSDF fusion of rendered depth and colour (supplementary,
+   mesh reconstruction).
+Each of 7-9 states its reading of the paper in its own section below.
 
 Readings of the paper where it is silent (all parameters of ``RenderParams``):
 EWA with 0.3 px^2 dilation and J clamped at 1.3 * tan(fov/2); alpha =
