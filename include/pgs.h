@@ -389,9 +389,10 @@ pgs_status pgs_scene_buffer(pgs_scene* s, int which, void** d_ptr, int64_t* capa
  * key/value pairs on bits [bit_lo, bit_hi) of the keys.  The sorted result
  * ends in (d_keys, d_vals); d_keys_alt / d_vals_alt are ping-pong buffers of
  * the same size.  Scratch must hold pgs_sort_scratch_bytes(n_max) bytes.  A
- * look-back wait that runs out (never expected) ORs bit PGS_ERR_TIMEOUT into
- * *d_err (device uint32, may be NULL) and the pass completes with an
- * unspecified order. */
+ * look-back wait that runs out (never expected) ORs bit PGS_ERR_TIMEOUT (the
+ * value 1u << PGS_ERR_TIMEOUT) into *d_err (device uint32, may be NULL) and
+ * the pass completes with an unspecified order.  *d_err must be 0 on entry:
+ * the passes poll it and stop waiting once that bit is set. */
 size_t pgs_sort_scratch_bytes(int64_t n_max);
 pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_alt, uint32_t* d_vals_alt,
                           const int64_t* d_n, int64_t n_max, int bit_lo, int bit_hi, void* d_scratch,
@@ -413,14 +414,22 @@ pgs_status pgs_exclusive_scan_u32(const uint32_t* d_in, const uint32_t* d_index,
  * the same stable order as pgs_sort_pairs.  All scratch (histograms,
  * look-back status, ping-pong keys and values) sits in one fixed array of
  * about 9.4 MB inside the library's device image, which every GPU that loads
- * the library holds until the process exits; nothing is allocated or freed.
- * The first call on a device looks up that array's device address (make it
- * before any stream capture).  Every call on a device shares the array and it
- * keeps the last call's contents, so calls that overlap on the GPU (other
- * streams, other host threads) race: serialise them.  Larger n is rejected with
- * PGS_ERR_INVALID_ARG and a message in pgs_last_error().  A look-back wait
- * that runs out ORs PGS_ERR_TIMEOUT into *d_err (device uint32, not cleared
- * by the call; may be NULL). */
+ * the library holds until the process exits; the call allocates and frees
+ * nothing.  Each call looks up that array's device address on the current
+ * device.  Warm-up: under CUDA's lazy module loading the FIRST call on a
+ * device may load the library's device code (which is when the array is
+ * reserved) and sets up the sort's launch once, so the allocation-free
+ * guarantee holds from the second call on; make one warm-up call (any
+ * n >= 1) per device first, and make it outside any stream capture.  Every
+ * call on a device shares the array and it keeps the last call's contents,
+ * so calls that overlap on the GPU (other streams, other host threads) race:
+ * serialise them.  n = 0 does nothing (keys and values may then be NULL).
+ * Larger n is rejected with PGS_ERR_INVALID_ARG and a message in
+ * pgs_last_error().  A look-back wait that runs out ORs bit PGS_ERR_TIMEOUT
+ * (the value 1u << PGS_ERR_TIMEOUT) into *d_err (device uint32, may be NULL,
+ * then an internal word is used).  A caller-supplied *d_err must be 0 on
+ * entry: the sort polls it and gives up its look-back waits early (leaving an
+ * unspecified order) once that bit is set. */
 pgs_status pgs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n, int bit_lo, int bit_hi,
                                   uint32_t* d_err, cudaStream_t stream);
 

@@ -480,8 +480,26 @@ class Scene:
 
 
 # ------------------------------------------------------------------ stand-alone stages
+def _check_sort_operands(keys: torch.Tensor, vals: torch.Tensor) -> None:
+    """The C entry points see only pointers and one count, so the binding
+    checks what they cannot: equal element counts, 4-byte elements,
+    contiguous CUDA tensors on the current device.  Raises ValueError."""
+    if keys.numel() != vals.numel():
+        raise ValueError(f"keys ({keys.numel()}) and values ({vals.numel()}) differ in length")
+    if keys.element_size() != 4 or vals.element_size() != 4:
+        raise ValueError(f"keys and values need 4-byte elements (got {keys.dtype}, {vals.dtype})")
+    if not (keys.is_contiguous() and vals.is_contiguous()):
+        raise ValueError("keys and values must be contiguous")
+    if keys.device.type != "cuda" or vals.device.type != "cuda":
+        raise ValueError(f"keys and values must be CUDA tensors (got {keys.device}, {vals.device})")
+    cur = torch.cuda.current_device()
+    if keys.device.index != cur or vals.device.index != cur:
+        raise ValueError(f"keys ({keys.device}) and values ({vals.device}) must sit on the current device cuda:{cur}")
+
+
 def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: int = 32):
     """Stable radix sort of int32-stored uint32 keys/values on device (in place)."""
+    _check_sort_operands(keys, vals)
     n = keys.numel()
     if n == 0:                       # one-element buffers; the library sees n = 0
         keys = torch.zeros(1, dtype=keys.dtype, device=keys.device)
@@ -503,7 +521,13 @@ def sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, 
                        err: Optional[torch.Tensor] = None):
     """In-place stable radix sort through pgs_sort_pairs_noalloc: the library
     allocates nothing (its scratch is a fixed array in its device image), for
-    callers that must not allocate device memory.  n <= NOALLOC_MAX_N."""
+    callers that must not allocate device memory.  n <= NOALLOC_MAX_N.  The
+    first call on a device may still load the library's device code (lazy
+    loading): warm up once per device.  ``err`` (int32, one element) must be
+    zero on entry."""
+    _check_sort_operands(keys, vals)
+    if keys.numel() == 0:
+        return keys, vals
     check(lib().pgs_sort_pairs_noalloc(_ptr(keys), _ptr(vals), keys.numel(), bit_lo, bit_hi, _ptr(err),
                                        _stream(None)))
     return keys, vals

@@ -519,18 +519,11 @@ __global__ void __launch_bounds__(32 * kBwdWarps) k_blend_bwd(const __grid_const
   }
 }
 
-// one resident wave: SMs x CTAs per SM, queried once per kernel instantiation
+// one resident wave on the current device: SMs x CTAs per SM (both cached per device)
 template <int TW, int TH, int NB, bool BWD, typename K>
 static int resident_grid(K kernel, int threads, int total) {
-  static int per_sm = -1, sms = 0;
-  if (per_sm < 0) {
-    int dev = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0) != cudaSuccess || per_sm < 1)
-      per_sm = 1;
-  }
-  return std::max(1, std::min(total, per_sm * sms));
+  const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(kernel), threads);
+  return std::max(1, std::min(total, per_sm * device_sm_count()));
 }
 
 template <int TW, int TH, int NB>

@@ -332,13 +332,7 @@ cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
   k_sort_hist<<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0]);
   k_sort_hist_scan<<<1, kRadix, 0, st>>>(s.hist, np);
   // persistent passes: one resident wave (tiles are taken from a counter)
-  static int per_sm = -1;
-  if (per_sm < 0) {
-    cudaFuncSetAttribute(k_sort_pass, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sort_pass, kSortThreads, 0) != cudaSuccess ||
-        per_sm < 1)
-      per_sm = 1;
-  }
+  const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_sort_pass), kSortThreads, 0, 100);
   const int pass_grid = (int)std::max(1ll, std::min((long long)per_sm * num_sms, (n_max + kSortTile - 1) / kSortTile));
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int p = 0; p < np; ++p) {

@@ -9,6 +9,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "pgs_internal.cuh"
@@ -74,6 +75,39 @@ cudaError_t dmalloc(T** p, size_t n) {
 
 namespace pgs {
 void set_last_error(const char* msg) { g_last_error = msg ? msg : ""; }
+
+namespace launch_cache {
+std::mutex mu;
+std::map<std::tuple<int, const void*, int, size_t>, int> occ;
+std::map<int, int> sms;
+}  // namespace launch_cache
+
+int resident_ctas_per_sm(const void* kernel, int threads, size_t smem, int carveout) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const auto key = std::make_tuple(dev, kernel, threads, smem);
+  std::lock_guard<std::mutex> lk(launch_cache::mu);
+  auto it = launch_cache::occ.find(key);
+  if (it != launch_cache::occ.end()) return it->second;
+  if (carveout >= 0) cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, carveout);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  launch_cache::occ[key] = per_sm;
+  return per_sm;
+}
+
+int device_sm_count() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  std::lock_guard<std::mutex> lk(launch_cache::mu);
+  auto it = launch_cache::sms.find(dev);
+  if (it != launch_cache::sms.end()) return it->second;
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  launch_cache::sms[dev] = n;
+  return n;
+}
 }  // namespace pgs
 
 struct pgs_scene {
@@ -789,9 +823,7 @@ pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_a
     return fail(PGS_ERR_INVALID_ARG, "bit range [%d, %d)", bit_lo, bit_hi);
   SortScratch ss = sort_scratch_layout(d_scratch, n_max);
   if (scratch_bytes < ss.bytes) return fail(PGS_ERR_INVALID_ARG, "scratch %zu < %zu bytes", scratch_bytes, ss.bytes);
-  int dev = 0, ns = 148;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+  const int ns = device_sm_count();
   PGS_CUDA(launch_sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, reinterpret_cast<const long long*>(d_n), n_max,
                              bit_lo, bit_hi, ss, d_err ? d_err : ss.err, kDefaultSpinLimit, ns, stream));
   return PGS_OK;

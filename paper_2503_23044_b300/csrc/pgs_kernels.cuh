@@ -42,6 +42,12 @@ struct SortScratch {
 
 // pgs_api.cu: message returned by pgs_last_error() on this host thread
 void set_last_error(const char* msg);
+// pgs_api.cu: resident CTAs per SM of `kernel` at `threads` threads (dynamic shared memory `smem`) on the
+// current device, at least 1.  Queried once per (device, kernel, threads, smem) and cached; thread-safe.
+// carveout >= 0 first sets the kernel's preferred shared-memory carveout (percent) on that device.
+int resident_ctas_per_sm(const void* kernel, int threads, size_t smem = 0, int carveout = -1);
+// pgs_api.cu: SM count of the current device (cached per device; thread-safe)
+int device_sm_count();
 
 // k_project.cu
 __global__ void k_project_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N, float4* rec,

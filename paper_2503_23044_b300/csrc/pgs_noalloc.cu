@@ -13,10 +13,17 @@
 // The array holds the device copy of n, the digit histograms, the look-back
 // status words and the ping-pong keys/values for at most kNoAllocMaxN pairs,
 // about 9.4 MB; every GPU that loads the library keeps it until the process
-// exits.  Host code cannot use the array's name as a device address, so the
-// address is looked up once per device with cudaGetSymbolAddress.
+// exits.  Host code cannot use the array's name as a device address, so every
+// call looks the address up with cudaGetSymbolAddress on the current device
+// (a cheap host call; nothing is cached, so the address is never stale after
+// a context is torn down and re-created).
+//
+// Under CUDA's lazy module loading the first call on a device can load this
+// file's device code, which is when the array is reserved, and it runs the
+// sort's one-time launch set-up (carveout and occupancy query).  The
+// allocation-free guarantee therefore holds from the second call on: warm up
+// each device with one call (any n >= 1) first, outside any stream capture.
 #include <cstdio>
-#include <mutex>
 
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
@@ -31,10 +38,6 @@ constexpr size_t kNoAllocBytes =
     kNoAllocHeader + ((kNoAllocSortBytes + 255) / 256) * 256 + 2 * kNoAllocPing;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
-
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
 
 __global__ void k_noalloc_setup(long long* d_n, long long n, uint32_t* err) {
   *d_n = n;
@@ -55,40 +58,27 @@ extern "C" {
 pgs_status pgs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n, int bit_lo, int bit_hi,
                                   uint32_t* d_err, cudaStream_t stream) {
   g_msg[0] = 0;
-  if (!d_keys || !d_vals) {
-    snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: null keys or values");
-    return fail_na(PGS_ERR_INVALID_ARG);
-  }
   if (n < 0 || n > kNoAllocMaxN) {
     snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: n = %lld is outside [0, %lld], the size of its fixed scratch",
              (long long)n, kNoAllocMaxN);
+    return fail_na(PGS_ERR_INVALID_ARG);
+  }
+  if (n > 0 && (!d_keys || !d_vals)) {
+    snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: null keys or values");
     return fail_na(PGS_ERR_INVALID_ARG);
   }
   if (bit_lo < 0 || bit_hi > 32 || bit_lo >= bit_hi) {
     snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: bit range [%d, %d)", bit_lo, bit_hi);
     return fail_na(PGS_ERR_INVALID_ARG);
   }
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
-    snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: cudaGetDevice: %s", cudaGetErrorString(e));
+  // set-up on the current device: the device address of the array (looked up on every call)
+  void* base = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&base, g_noalloc_scratch);
+  if (e != cudaSuccess || !base) {
+    snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
     return fail_na(PGS_ERR_CUDA);
   }
-  void* base = nullptr;
-  {
-    // set-up, once per device, with that device current: the device address of the array
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-      void* p = nullptr;
-      e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess || !p) {
-        snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-        return fail_na(PGS_ERR_CUDA);
-      }
-      g_addr[dev] = p;
-    }
-    base = g_addr[dev];
-  }
+  if (n == 0) return PGS_OK;
   unsigned char* b = static_cast<unsigned char*>(base);
   long long* d_n = reinterpret_cast<long long*>(b);
   uint32_t* own_err = reinterpret_cast<uint32_t*>(b + 8);
@@ -98,8 +88,7 @@ pgs_status pgs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n,
   pgs::SortScratch ss = pgs::sort_scratch_layout(sort_base, kNoAllocMaxN);
   // n and the error word start each call fresh (the array keeps the last call's contents)
   k_noalloc_setup<<<1, 1, 0, stream>>>(d_n, (long long)n, own_err);
-  int ns = 148;
-  cudaDeviceGetAttribute(&ns, cudaDevAttrMultiProcessorCount, dev);
+  const int ns = pgs::device_sm_count();
   e = pgs::launch_sort_pairs(d_keys, d_vals, alt_k, alt_v, d_n, kNoAllocMaxN, bit_lo, bit_hi, ss,
                              d_err ? d_err : own_err, 1u << 20, ns, stream);
   if (e == cudaSuccess) e = cudaGetLastError();

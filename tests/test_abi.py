@@ -99,3 +99,20 @@ def test_new_entry_points_reject_null_arguments_without_gpu():
     assert L.pgs_tsdf_integrate(None, None, 1, None, None, ctypes.byref(vol), None, None, None,
                                 None) == B.PGS_ERR_INVALID_ARG
     assert b"null" in L.pgs_last_error()
+
+
+def test_sort_bindings_reject_operands_the_c_side_cannot_check():
+    """The sort entry points receive pointers and one count: the binding must
+    refuse mismatched lengths, element sizes other than 4 bytes and tensors
+    not on the current CUDA device before any call into the library."""
+    import torch
+    k32 = torch.zeros(8, dtype=torch.int32)
+    for fn in (B.sort_pairs, B.sort_pairs_noalloc):
+        with pytest.raises(ValueError, match="differ in length"):
+            fn(k32, torch.zeros(7, dtype=torch.int32))
+        with pytest.raises(ValueError, match="4-byte"):
+            fn(torch.zeros(8, dtype=torch.int16), torch.zeros(8, dtype=torch.int16))
+        with pytest.raises(ValueError, match="4-byte"):
+            fn(k32, torch.zeros(8, dtype=torch.int64))
+        with pytest.raises(ValueError, match="CUDA"):
+            fn(k32, torch.zeros(8, dtype=torch.int32))

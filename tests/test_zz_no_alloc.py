@@ -41,6 +41,33 @@ def test_noalloc_sort_matches_regular_sort_on_two_calls_in_a_row():
         assert torch.equal(v_na, v_ref), (n, bits)
 
 
+def test_noalloc_sort_allocates_nothing_after_the_warm_up_call():
+    """After one warm-up call on the device (which may load the library's
+    device code under lazy loading), a call changes neither the device's free
+    memory nor torch's allocated bytes."""
+    err = torch.zeros(1, dtype=torch.int32, device="cuda")
+    keys, vals = _pairs(300_000, 7, 1 << 32)
+    k = torch.tensor(keys.view(np.int32), device="cuda")
+    v = torch.tensor(vals.view(np.int32), device="cuda")
+    B.sort_pairs_noalloc(k.clone(), v.clone(), err=err)          # warm-up
+    k_ref, v_ref, _ = B.sort_pairs(k.clone(), v.clone())
+    torch.cuda.synchronize()
+    free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    B.sort_pairs_noalloc(k, v, err=err)
+    torch.cuda.synchronize()
+    free1, alloc1 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+    assert (free0, alloc0) == (free1, alloc1), (free0 - free1, alloc1 - alloc0)
+    assert int(err.item()) == 0
+    assert torch.equal(k, k_ref) and torch.equal(v, v_ref)
+
+
+def test_noalloc_sort_of_nothing():
+    k = torch.zeros(0, dtype=torch.int32, device="cuda")
+    v = torch.zeros(0, dtype=torch.int32, device="cuda")
+    assert B.sort_pairs_noalloc(k, v)[0].numel() == 0
+    B.check(B.lib().pgs_sort_pairs_noalloc(None, None, 0, 0, 32, None, None))   # n = 0 with null pointers
+
+
 def test_noalloc_sort_rejects_sizes_beyond_its_scratch():
     n = B.NOALLOC_MAX_N + 1
     k = torch.zeros(n, dtype=torch.int32, device="cuda")
