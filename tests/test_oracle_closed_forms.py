@@ -362,3 +362,99 @@ def test_stop_and_skip_rules():
     sc = explicit([[0, 0, 2.0]], [[math.log(0.05)] * 3], [[1, 0, 0, 0]], [0.0035], [[1, 1, 1]], cam)
     out = O.render(sc, RP)["views"][0]
     assert out["rgb"].abs().max().item() == 0.0 and out["n_gaussians"] == 0
+
+
+# ----------------------------------------------------------------- depth-normal (consistency term) and block cull
+def test_depth_normal_of_a_tilted_plane_seen_off_axis():
+    """The depth map of the plane n . X = d (camera frame) seen by a camera
+    with fx != fy and an off-centre principal point is D(u, v) = d / (n . r),
+    r = ((u + 1/2 - cx) / fx, (v + 1/2 - cy) / fy, 1).  Back-projecting it and
+    crossing the central differences must give the plane normal (facing the
+    camera) at every interior pixel.  Dropping the depth factor, the +1/2
+    pixel centre, or using fx for fy bends the back-projected surface and
+    fails."""
+    n = np.array([0.3, -0.5, -0.8])
+    n /= np.linalg.norm(n)
+    d = -3.0                                    # n . X = d with X in front of the camera (n . X < 0: faces it)
+    H, W = 23, 31
+    cam = dict(fx=41.0, fy=29.0, cx=9.3, cy=15.8, W=W, H=H)
+    v, u = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
+    r = np.stack([(u - cam["cx"]) / cam["fx"], (v - cam["cy"]) / cam["fy"], np.ones_like(u)], 0)
+    D = d / np.einsum("i,ijk->jk", n, r)
+    assert (D > 0).all()
+    Nd, valid = O.depth_normal(torch.tensor(D, dtype=O.DT), cam)
+    assert bool(valid[1:-1, 1:-1].all()) and not bool(valid[0].any()) and not bool(valid[:, -1].any())
+    err = (Nd[:, 1:-1, 1:-1] - torch.tensor(n, dtype=O.DT)[:, None, None]).abs().max().item()
+    assert err < 1e-9, err
+
+    def wrong(fn_r):
+        P = D[None] * fn_r
+        ex = P[:, 1:-1, 2:] - P[:, 1:-1, :-2]
+        ey = P[:, 2:, 1:-1] - P[:, :-2, 1:-1]
+        c = np.cross(ex, ey, axis=0)
+        c /= np.linalg.norm(c, axis=0)
+        return np.abs(np.abs(c) - np.abs(n)[:, None, None]).max()
+    # the same construction with each plausible slip is far from the normal (the test can see them)
+    r_no_half = np.stack([(u - 0.5 - cam["cx"]) / cam["fx"], (v - 0.5 - cam["cy"]) / cam["fy"], np.ones_like(u)], 0)
+    r_fx = np.stack([(u - cam["cx"]) / cam["fx"], (v - cam["cy"]) / cam["fx"], np.ones_like(u)], 0)
+    assert wrong(r_no_half) > 1e-3 and wrong(r_fx) > 1e-2 and wrong(r / D[None]) > 1e-2
+
+
+def _anisotropic_scene(seed=11):
+    """Rotated needle-like Gaussians (axis ratios 10-30) scattered over a
+    96 x 80 frame, so that many 32 x 32 blocks see only a long tail."""
+    rng = np.random.default_rng(seed)
+    n = 60
+    W, H, f = 96, 80, 90.0
+    cam = synth.identity_camera(W, H, f)
+    z = rng.uniform(2.0, 4.0, n)
+    means = np.stack([rng.uniform(-1.2, 1.2, n) * z / 2.5, rng.uniform(-1.0, 1.0, n) * z / 2.5, z], 1)
+    big = rng.uniform(-1.6, -1.0, n)
+    ratio = np.log(rng.uniform(10.0, 30.0, n))
+    log_scales = np.stack([big, big - ratio, big - ratio - rng.uniform(0, 0.5, n)], 1)
+    quats = np.array([quat_wxyz(Rotation.from_euler("zyx", rng.uniform(-math.pi, math.pi, 3))) for _ in range(n)])
+    opac = rng.uniform(0.3, 0.99, n)
+    colors = rng.uniform(0.0, 1.0, (n, 3))
+    return explicit(means, log_scales, quats, opac, colors, cam)
+
+
+def test_block_cull_keeps_every_contributor_of_anisotropic_gaussians(monkeypatch):
+    """The oracle processes pixels in 32 x 32 blocks and keeps, per block, the
+    Gaussians whose bound o exp(-|delta|^2 / (2 lambda_max)) can reach
+    alpha >= 1/255 there.  Rendering the same rotated, strongly anisotropic
+    scene with that cull and with no cull at all (every Gaussian kept in every
+    block) must give the same FP64 images and contributor counts.  The same
+    bound taken with the smaller eigenvalue culls contributors and must show."""
+    import oracle.pgs_oracle as OP
+    sc = _anisotropic_scene()
+    culled = O.render(sc, RP)["views"][0]
+    kept_per_block = []
+    real = OP._reject_rect
+
+    def count(proj, keep, x0, x1, y0, y1, rp):
+        k = real(proj, keep, x0, x1, y0, y1, rp)
+        kept_per_block.append((int(k.sum()), int(keep.sum())))
+        return k
+    monkeypatch.setattr(OP, "_reject_rect", count)
+    O.render(sc, RP)
+    assert any(a < b for a, b in kept_per_block), "the cull removed nothing: the scene does not exercise it"
+    monkeypatch.setattr(OP, "_reject_rect", lambda proj, keep, *a: keep)
+    full = O.render(sc, RP)["views"][0]
+    for k in ("rgb", "normal", "depth", "D", "T_final"):
+        assert (culled[k] - full[k]).abs().max().item() <= 1e-12, k
+    assert torch.equal(culled["n_contrib"], full["n_contrib"])
+    assert int(full["n_contrib"].sum()) > 0
+
+    def lam_min_cull(proj, keep, x0, x1, y0, y1, rp):     # the plausible slip: the smaller eigenvalue
+        with torch.no_grad():
+            m = proj["mean2d"]
+            a, b, c = proj["cov"].unbind(-1)
+            lam = 0.5 * (a + c) - torch.sqrt(torch.clamp(0.25 * (a - c) ** 2 + b * b, min=0.0))
+            ddx = torch.clamp(torch.maximum(x0 - m[:, 0], m[:, 0] - x1), min=0.0)
+            ddy = torch.clamp(torch.maximum(y0 - m[:, 1], m[:, 1] - y1), min=0.0)
+            bound = proj["opacity"] * torch.exp(-0.5 * (ddx * ddx + ddy * ddy) / lam)
+            return keep & (bound >= rp.alpha_min * (1.0 - 1e-6))
+    monkeypatch.setattr(OP, "_reject_rect", lam_min_cull)
+    slip = O.render(sc, RP)["views"][0]
+    assert not torch.equal(slip["n_contrib"], full["n_contrib"])
+    assert (slip["rgb"] - full["rgb"]).abs().max().item() > 1e-3
