@@ -68,6 +68,7 @@ AMB_GAUSS = 1e-6
 
 @dataclasses.dataclass
 class RenderParams:
+    decode: str = "fp64"            # decoder arithmetic: "fp64", "bf16" or "bf16_1pass" (see ``decode``)
     near: float = 0.01
     dilation: float = 0.3
     alpha_min: float = 1.0 / 255.0
@@ -139,11 +140,29 @@ def lod_active(x: torch.Tensor, level: torch.Tensor, cam: dict, rp: RenderParams
 
 
 # ------------------------------------------------------------------ decoder (Eq. 4)
-def decode(anchors: dict, mlp: dict, cam: dict, idx: torch.Tensor, in_dim: int = 35) -> dict:
+def bf16_round(x: torch.Tensor) -> torch.Tensor:
+    """Round to the nearest BF16 value (8 significant bits, ties to even),
+    computed in FP64 as the definition: x = m 2^e with 0.5 <= |m| < 1, keep
+    round(m 2^8) / 2^8.  The gradient passes straight through (d round(x)/dx
+    taken as 1), which is the gradient of the rounded forward's arithmetic."""
+    xd = x.detach()
+    m, e = torch.frexp(xd)
+    r = torch.ldexp(torch.round(m * 256.0) / 256.0, e)       # torch.round: half to even
+    return x + (r - xd)
+
+
+def decode(anchors: dict, mlp: dict, cam: dict, idx: torch.Tensor, in_dim: int = 35,
+           precision: str = "fp64") -> dict:
     """Decode the anchors ``idx`` into n = 10 neural Gaussians each.
 
     Input X = [F_v (32), unit direction (x_v - o_c)/|.| (3)] (+ distance if
-    ``in_dim`` = 36); H = ReLU(W1 X + b1); Z = W2 H + b2 (110)."""
+    ``in_dim`` = 36); H = ReLU(W1 X + b1); Z = W2 H + b2 (110).
+
+    The paper states no precision for F_de.  ``precision`` selects the
+    arithmetic the GPU's decoder forms define, emulated in FP64:
+    "fp64" exact; "bf16" the colour outputs Z[10:40] from BF16-rounded H and
+    W2 (one BF16 pass), everything else exact; "bf16_1pass" X, W1, H and W2
+    all rounded to BF16 before their products (biases exact)."""
     x = anchors["x"][idx]
     F = anchors["feat"][idx]
     l = torch.exp(anchors["log_l"][idx])
@@ -154,8 +173,17 @@ def decode(anchors: dict, mlp: dict, cam: dict, idx: torch.Tensor, in_dim: int =
     if in_dim == 36:
         parts.append(dist)
     X = torch.cat(parts, -1)
-    H = torch.relu(X @ mlp["W1"].T + mlp["b1"])
-    Z = H @ mlp["W2"].T + mlp["b2"]
+    if precision == "bf16_1pass":
+        H = torch.relu(bf16_round(X) @ bf16_round(mlp["W1"]).T + mlp["b1"])
+        Z = bf16_round(H) @ bf16_round(mlp["W2"]).T + mlp["b2"]
+    else:
+        H = torch.relu(X @ mlp["W1"].T + mlp["b1"])
+        Z = H @ mlp["W2"].T + mlp["b2"]
+        if precision == "bf16":
+            Zc = bf16_round(H) @ bf16_round(mlp["W2"][10:40]).T + mlp["b2"][10:40]
+            Z = torch.cat([Z[:, :10], Zc, Z[:, 40:]], 1)
+        elif precision != "fp64":
+            raise ValueError(f"decoder precision {precision!r}")
     A = x.shape[0]
     opacity = torch.sigmoid(Z[:, 0:10])
     color = torch.sigmoid(Z[:, 10:40]).reshape(A, N_OFF, 3)
@@ -389,7 +417,7 @@ def gaussians_for_view(scene: dict, leaves: dict, cam: dict, rp: RenderParams, i
     idx = torch.nonzero(active).flatten()
     anchors = dict(x=leaves["x"], feat=leaves["feat"], log_l=leaves["log_l"], offsets=leaves["offsets"])
     mlp = {k: leaves[k] for k in ("W1", "b1", "W2", "b2")}
-    dec = decode(anchors, mlp, cam, idx, in_dim)
+    dec = decode(anchors, mlp, cam, idx, in_dim, rp.decode)
     dec["anchor_idx"] = idx
     dec["lod_amb"] = amb
     return dec
