@@ -51,7 +51,7 @@ enum pgs_status_code {
   PGS_ERR_INVALID_ARG = 1,   /* bad pointer, size or descriptor field */
   PGS_ERR_CAPACITY = 2,      /* rows / pairs exceeded the capacities given at create */
   PGS_ERR_TIMEOUT = 3,       /* a bounded device-side wait (sort look-back) ran out */
-  PGS_ERR_NONFINITE = 4,     /* non-finite value met in a loss or gradient */
+  PGS_ERR_NONFINITE = 4,     /* non-finite value met in a parameter, a loss or a gradient */
   PGS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
   PGS_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
 };
@@ -63,7 +63,18 @@ enum pgs_status_code {
 #define PGS_OUT_DIM 110
 
 enum pgs_mode { PGS_MODE_EXPLICIT = 0, PGS_MODE_ANCHOR = 1 };
-enum pgs_decode_precision { PGS_DECODE_FP32 = 0, PGS_DECODE_BF16 = 1 };
+/* Arithmetic of the decoder F_de (Eq. 4; the paper does not state one).
+ *  FP32:       FP32 SIMT.
+ *  BF16:       the 5th-generation tensor cores, BF16 operands and FP32
+ *              accumulation.  The colour heads take one BF16 pass (their error
+ *              reaches the image through a sigmoid and stays below 1e-3);
+ *              layer 1 and the opacity, scale and rotation heads, which decide
+ *              the blend weights, the smallest-scale normal axis of Eq. 6 and
+ *              the normalised rotation, use an exact three-piece BF16 split of
+ *              both operands (six products per layer: FP32-accurate).
+ *  BF16_1PASS: every product in one BF16 pass (a precision study: its normal
+ *              and depth maps move by up to ~1e-1, far past the colour bar). */
+enum pgs_decode_precision { PGS_DECODE_FP32 = 0, PGS_DECODE_BF16 = 1, PGS_DECODE_BF16_1PASS = 2 };
 
 typedef struct pgs_camera {
   float R[9];        /* world -> camera rotation, row-major */
@@ -249,6 +260,20 @@ enum pgs_stage {
   PGS_N_STAGES = 12
 };
 pgs_status pgs_set_profiling(pgs_scene* s, int enable);
+
+/* Bounded device waits (no counterpart in the paper).  The only spin-waits of
+ * the step are the look-backs of the onesweep sorts (depth, tile and queue
+ * order): each gives up after spin_limit polls (0 restores the default,
+ * 2^20), raises PGS_ERR_TIMEOUT for pgs_read_status and leaves that sort's
+ * output unspecified; the step then continues on safe stand-ins (Gaussians in
+ * index order, no pairs, tiles in index order), so every later call of the
+ * step returns and the context stays usable, but the images and gradients of
+ * that step are meaningless.  withhold_tile is a failure-path test hook: the
+ * onesweep tile (2048 keys) with this index never publishes its look-back
+ * status in any pass, so the next tile's wait runs out; PGS_NO_WITHHELD_TILE
+ * (the default) publishes every tile.  Applies to later calls on this scene. */
+#define PGS_NO_WITHHELD_TILE 0xffffffffu
+pgs_status pgs_scene_set_wait_limits(pgs_scene* s, uint32_t spin_limit, uint32_t withhold_tile);
 pgs_status pgs_get_stage_times(pgs_scene* s, float* ms, int n);
 
 /* Launch-shape autotuner (no counterpart in the paper: it only picks how the

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_HERE, "libpgs.so")
 
 PGS_OK, PGS_ERR_INVALID_ARG, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE, PGS_ERR_CUDA, PGS_ERR_UNSUPPORTED = range(7)
 MODE_EXPLICIT, MODE_ANCHOR = 0, 1
-DECODE_FP32, DECODE_BF16 = 0, 1
+DECODE_FP32, DECODE_BF16, DECODE_BF16_1PASS = 0, 1, 2
 MAX_VIEWS = 32
 
 
@@ -124,7 +124,8 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_loss_grad", "pgs_backward", "pgs_read_status", "pgs_get_stats", "pgs_set_profiling",
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
-                "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad", "pgs_tsdf_integrate")
+                "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad", "pgs_tsdf_integrate",
+                "pgs_scene_set_wait_limits")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad",
           "prior", "ncc", "tsdf")
 
@@ -152,6 +153,7 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_read_status.argtypes = [vp, vp]
     L.pgs_get_stats.argtypes = [vp, P(Stats), vp]
     L.pgs_set_profiling.argtypes = [vp, i32]
+    L.pgs_scene_set_wait_limits.argtypes = [vp, C.c_uint32, C.c_uint32]
     L.pgs_get_stage_times.argtypes = [vp, P(C.c_float), i32]
     L.pgs_scene_buffer.argtypes = [vp, i32, P(vp), P(i64)]
     L.pgs_sort_scratch_bytes.argtypes = [i64]
@@ -461,6 +463,12 @@ class Scene:
         check(lib().pgs_get_stats(self.handle, C.byref(st), _stream(stream)))
         return st
 
+    def set_wait_limits(self, spin_limit: int = 0, withhold_tile: Optional[int] = None) -> None:
+        """pgs_scene_set_wait_limits: polls before a sort look-back gives up (0 = default) and the
+        failure-path hook that withholds one onesweep tile's status (None = publish every tile)."""
+        check(lib().pgs_scene_set_wait_limits(self.handle, spin_limit,
+                                              NO_WITHHELD_TILE if withhold_tile is None else withhold_tile))
+
     def set_profiling(self, on: bool) -> None:
         check(lib().pgs_set_profiling(self.handle, 1 if on else 0))
 
@@ -515,6 +523,7 @@ def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: 
 
 
 NOALLOC_MAX_N = 1 << 20
+NO_WITHHELD_TILE = 0xFFFFFFFF
 
 
 def sort_pairs_noalloc(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: int = 32,

@@ -9,146 +9,13 @@
 // summed over the views of the batch with atomics; the decoder's weight
 // gradients, summed over all visible (view, anchor) rows, go through a
 // split-row reduction with fixed-order partial sums.
+#include <cuda_bf16.h>
+
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
+#include "pgs_backward.cuh"
 
 namespace pgs {
-
-__device__ __forceinline__ float sigm(float x) { return 1.f / (1.f + expf(-x)); }
-
-struct ProjGrad {
-  float dmu[3], ds[3], dq[4], dop, dcol[3];
-};
-
-// Chain the 13 per-Gaussian-view gradients back to (mu, s, unit q, opacity, colour).
-__device__ void project_backward(const BatchDev& b, const ViewDev& v, const float mu[3], const float s[3],
-                                 const float q[4], const float* gr, ProjGrad& out) {
-  const ParamsDev& p = b.p;
-  const float* W = v.R;
-  const float x = W[0] * mu[0] + W[1] * mu[1] + W[2] * mu[2] + v.t[0];
-  const float y = W[3] * mu[0] + W[4] * mu[1] + W[5] * mu[2] + v.t[1];
-  const float z = W[6] * mu[0] + W[7] * mu[1] + W[8] * mu[2] + v.t[2];
-  const float iz = 1.f / z, iz2 = iz * iz;
-  const float xz = x * iz, yz = y * iz;
-  const bool clx = xz < -v.lim_x || xz > v.lim_x, cly = yz < -v.lim_y || yz > v.lim_y;
-  const float txz = fminf(fmaxf(xz, -v.lim_x), v.lim_x), tyz = fminf(fmaxf(yz, -v.lim_y), v.lim_y);
-  const float J00 = v.fx * iz, J02 = -v.fx * txz * iz, J11 = v.fy * iz, J12 = -v.fy * tyz * iz;
-  float Rg[9];
-  quat_to_rot(q[0], q[1], q[2], q[3], Rg);
-  float T[2][3];
-  for (int c = 0; c < 3; ++c) {
-    T[0][c] = J00 * W[c] + J02 * W[6 + c];
-    T[1][c] = J11 * W[3 + c] + J12 * W[6 + c];
-  }
-  float M[3][3];  // M = Rg diag(s)
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) M[i][k] = Rg[3 * i + k] * s[k];
-  float U[2][3];  // U = T M
-  for (int r = 0; r < 2; ++r)
-    for (int k = 0; k < 3; ++k) U[r][k] = T[r][0] * M[0][k] + T[r][1] * M[1][k] + T[r][2] * M[2][k];
-  float a = p.dilation, bb = 0.f, c = p.dilation;
-  for (int k = 0; k < 3; ++k) {
-    a += U[0][k] * U[0][k];
-    bb += U[0][k] * U[1][k];
-    c += U[1][k] * U[1][k];
-  }
-  const float det = a * c - bb * bb, idet = 1.f / det;
-  const float QA = c * idet, QB = -bb * idet, QC = a * idet;
-  // dL/dcov = -Q G Q, G = [[dA, dB/2],[dB/2, dC]]
-  const float gA = gr[2], gB = 0.5f * gr[3], gC = gr[4];
-  const float t00 = QA * gA + QB * gB, t01 = QA * gB + QB * gC;
-  const float t10 = QB * gA + QC * gB, t11 = QB * gB + QC * gC;
-  const float D00 = -(t00 * QA + t01 * QB), D01 = -(t00 * QB + t01 * QC), D11 = -(t10 * QB + t11 * QC);
-  // dL/dU = 2 D U (D symmetric with off-diagonal D01)
-  float dU[2][3];
-  for (int k = 0; k < 3; ++k) {
-    dU[0][k] = 2.f * (D00 * U[0][k] + D01 * U[1][k]);
-    dU[1][k] = 2.f * (D01 * U[0][k] + D11 * U[1][k]);
-  }
-  // U = T M: dT = dU M^T, dM = T^T dU
-  float dT[2][3], dM[3][3];
-  for (int r = 0; r < 2; ++r)
-    for (int cc = 0; cc < 3; ++cc) dT[r][cc] = dU[r][0] * M[cc][0] + dU[r][1] * M[cc][1] + dU[r][2] * M[cc][2];
-  for (int i = 0; i < 3; ++i)
-    for (int k = 0; k < 3; ++k) dM[i][k] = T[0][i] * dU[0][k] + T[1][i] * dU[1][k];
-  // M = Rg diag(s)
-  float dRg[9];
-  for (int k = 0; k < 3; ++k) {
-    out.ds[k] = dM[0][k] * Rg[k] + dM[1][k] * Rg[3 + k] + dM[2][k] * Rg[6 + k];
-    for (int i = 0; i < 3; ++i) dRg[3 * i + k] = dM[i][k] * s[k];
-  }
-  // T = J W: dJ = dT W^T (entries (0,0), (0,2), (1,1), (1,2) are live)
-  const float dJ00 = dT[0][0] * W[0] + dT[0][1] * W[1] + dT[0][2] * W[2];
-  const float dJ02 = dT[0][0] * W[6] + dT[0][1] * W[7] + dT[0][2] * W[8];
-  const float dJ11 = dT[1][0] * W[3] + dT[1][1] * W[4] + dT[1][2] * W[5];
-  const float dJ12 = dT[1][0] * W[6] + dT[1][1] * W[7] + dT[1][2] * W[8];
-  // camera-frame mean: 2D mean, J
-  float dx = v.fx * iz * gr[0];
-  float dy = v.fy * iz * gr[1];
-  float dz = -v.fx * x * iz2 * gr[0] - v.fy * y * iz2 * gr[1];
-  dz += -v.fx * iz2 * dJ00 - v.fy * iz2 * dJ11;
-  if (clx) dz += v.fx * txz * iz2 * dJ02;
-  else { dx += -v.fx * iz2 * dJ02; dz += 2.f * v.fx * x * iz2 * iz * dJ02; }
-  if (cly) dz += v.fy * tyz * iz2 * dJ12;
-  else { dy += -v.fy * iz2 * dJ12; dz += 2.f * v.fy * y * iz2 * iz * dJ12; }
-  // normal n_c = sgn W Rg[:,k] and d = n_c . mu_c
-  int k = 0;
-  if (s[1] < s[k]) k = 1;
-  if (s[2] < s[k]) k = 2;
-  const float nw0 = Rg[k], nw1 = Rg[3 + k], nw2 = Rg[6 + k];
-  float n0 = W[0] * nw0 + W[1] * nw1 + W[2] * nw2;
-  float n1 = W[3] * nw0 + W[4] * nw1 + W[5] * nw2;
-  float n2 = W[6] * nw0 + W[7] * nw1 + W[8] * nw2;
-  const float sg = (n0 * x + n1 * y + n2 * z > 0.f) ? -1.f : 1.f;
-  n0 *= sg; n1 *= sg; n2 *= sg;
-  const float gd = gr[9];
-  const float gn0 = gr[10] + gd * x, gn1 = gr[11] + gd * y, gn2 = gr[12] + gd * z;
-  dx += gd * n0; dy += gd * n1; dz += gd * n2;
-  // dRg[:,k] += sg W^T gn
-  dRg[k] += sg * (W[0] * gn0 + W[3] * gn1 + W[6] * gn2);
-  dRg[3 + k] += sg * (W[1] * gn0 + W[4] * gn1 + W[7] * gn2);
-  dRg[6 + k] += sg * (W[2] * gn0 + W[5] * gn1 + W[8] * gn2);
-  // world mean
-  out.dmu[0] = W[0] * dx + W[3] * dy + W[6] * dz;
-  out.dmu[1] = W[1] * dx + W[4] * dy + W[7] * dz;
-  out.dmu[2] = W[2] * dx + W[5] * dy + W[8] * dz;
-  // rotation matrix of a unit quaternion (w, x, y, z)
-  const float qw = q[0], qx = q[1], qy = q[2], qz = q[3];
-  out.dq[0] = 2.f * (-qz * dRg[1] + qy * dRg[2] + qz * dRg[3] - qx * dRg[5] - qy * dRg[6] + qx * dRg[7]);
-  out.dq[1] = 2.f * (qy * dRg[1] + qz * dRg[2] + qy * dRg[3] - 2.f * qx * dRg[4] - qw * dRg[5] + qz * dRg[6] +
-                     qw * dRg[7] - 2.f * qx * dRg[8]);
-  out.dq[2] = 2.f * (-2.f * qy * dRg[0] + qx * dRg[1] + qw * dRg[2] + qx * dRg[3] + qz * dRg[5] - qw * dRg[6] +
-                     qz * dRg[7] - 2.f * qy * dRg[8]);
-  out.dq[3] = 2.f * (-2.f * qz * dRg[0] - qw * dRg[1] + qx * dRg[2] + qw * dRg[3] - 2.f * qz * dRg[4] +
-                     qy * dRg[5] + qx * dRg[6] + qy * dRg[7]);
-  out.dop = gr[5];
-  out.dcol[0] = gr[6]; out.dcol[1] = gr[7]; out.dcol[2] = gr[8];
-}
-
-// d normalise(q) -> d q_raw ; q_unit = q / |q| (identity substitute has no gradient)
-__device__ __forceinline__ void quat_norm_backward(const float qr[4], float qn, const float dqu[4], float dq[4]) {
-  if (qn < 1e-12f) { dq[0] = dq[1] = dq[2] = dq[3] = 0.f; return; }
-  const float iq = 1.f / qn;
-  const float u[4] = {qr[0] * iq, qr[1] * iq, qr[2] * iq, qr[3] * iq};
-  const float dt = u[0] * dqu[0] + u[1] * dqu[1] + u[2] * dqu[2] + u[3] * dqu[3];
-  for (int i = 0; i < 4; ++i) dq[i] = (dqu[i] - u[i] * dt) * iq;
-}
-
-__device__ __forceinline__ bool load_grad(const float* __restrict__ grad, long long g, float gr[13]) {
-  const float4* p = reinterpret_cast<const float4*>(grad + g * 16);
-  const float4 a = p[0], b = p[1], c = p[2], d = p[3];
-  gr[0] = a.x; gr[1] = a.y; gr[2] = a.z; gr[3] = a.w;
-  gr[4] = b.x; gr[5] = b.y; gr[6] = b.z; gr[7] = b.w;
-  gr[8] = c.x; gr[9] = c.y; gr[10] = c.z; gr[11] = c.w;
-  gr[12] = d.x;
-  bool nz = false;
-  for (int i = 0; i < 13; ++i) nz |= gr[i] != 0.f;
-  return nz;
-}
-
-__device__ __forceinline__ void add_if(float* p, float v) {
-  if (p && v != 0.f) atomicAdd(p, v);
-}
 
 // ---------------------------------------------------------------- explicit mode
 __global__ void __launch_bounds__(128) k_project_bwd_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P,
@@ -193,10 +60,24 @@ struct __align__(16) MlpSmemB {
 };
 static_assert(kMaxIn % 4 == 0 && kHidden % 4 == 0, "float4 rows");
 
-// z = b2[o] + W2[o] . H (one decoder output, weight row read as float4)
-__device__ __forceinline__ float w2_dot(const MlpSmemB& m, int o, const float (&H)[kHidden]) {
+__device__ __forceinline__ float bf16r(float x) { return __bfloat162float(__float2bfloat16_rn(x)); }
+__device__ __forceinline__ bool colour_out(int o) { return o >= kNOff && o < 4 * kNOff; }
+
+// z = b2[o] + W2[o] . H (one decoder output, weight row read as float4); with
+// round_h the hidden values are rounded to BF16 first (the one-pass colour
+// heads of the BF16 decoder, whose weight rows are stored rounded)
+__device__ __forceinline__ float w2_dot(const MlpSmemB& m, int o, const float (&H)[kHidden], bool round_h) {
   const float4* w = reinterpret_cast<const float4*>(m.W2[o]);
   float acc = m.b2[o];
+  if (round_h) {
+#pragma unroll
+    for (int q = 0; q < kHidden / 4; ++q) {
+      const float4 ww = w[q];
+      acc = fmaf(ww.x, bf16r(H[4 * q]), acc); acc = fmaf(ww.y, bf16r(H[4 * q + 1]), acc);
+      acc = fmaf(ww.z, bf16r(H[4 * q + 2]), acc); acc = fmaf(ww.w, bf16r(H[4 * q + 3]), acc);
+    }
+    return acc;
+  }
 #pragma unroll
   for (int q = 0; q < kHidden / 4; ++q) {
     const float4 ww = w[q];
@@ -220,7 +101,11 @@ __device__ __forceinline__ void w2_axpy(const MlpSmemB& m, int o, float dz, floa
 // outputs), run the projection backward of its 10 Gaussians, and carry the
 // gradient back through the decoder: dZ (11 entries per Gaussian, written to
 // the weight-gradient scratch as they are formed), dH accumulated in registers
-// Gaussian by Gaussian, dX = W1^T (dH . [H > 0]).
+// Gaussian by Gaussian, dX = W1^T (dH . [H > 0]).  The recomputed forward
+// rounds where the rendered one did (b.p.decode): the BF16 decoder's colour
+// heads multiply BF16-rounded H and W2 rows; the one-pass form rounds X, W1,
+// H and W2.  The gradient passes straight through each rounding, i.e. the
+// backward multiplies the same rounded operands the forward multiplied.
 __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A,
                                                     pgs_mlp_ptrs Wt, const uint32_t* __restrict__ rows,
                                                     const long long* __restrict__ n_rows_p, long long cap,
@@ -229,12 +114,18 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
                                                     float* __restrict__ sc_dH, float* __restrict__ sc_X, uint32_t* err) {
   __shared__ MlpSmemB m;
   const int in_dim = b.p.in_dim;
+  const bool one_pass = b.p.decode == PGS_DECODE_BF16_1PASS;
+  const bool round_colour = b.p.decode == PGS_DECODE_BF16;
   for (int t = threadIdx.x; t < kHidden * kMaxIn; t += blockDim.x) {
     const int i = t / kMaxIn, j = t % kMaxIn;
-    m.W1[i][j] = j < in_dim ? Wt.W1[i * in_dim + j] : 0.f;
+    const float w = j < in_dim ? Wt.W1[i * in_dim + j] : 0.f;
+    m.W1[i][j] = one_pass ? bf16r(w) : w;
   }
   for (int t = threadIdx.x; t < kHidden; t += blockDim.x) m.b1[t] = Wt.b1[t];
-  for (int t = threadIdx.x; t < kOut * kHidden; t += blockDim.x) m.W2[t / kHidden][t % kHidden] = Wt.W2[t];
+  for (int t = threadIdx.x; t < kOut * kHidden; t += blockDim.x) {
+    const float w = Wt.W2[t];
+    m.W2[t / kHidden][t % kHidden] = (one_pass || (round_colour && colour_out(t / kHidden))) ? bf16r(w) : w;
+  }
   for (int t = threadIdx.x; t < kOut; t += blockDim.x) m.b2[t] = Wt.b2[t];
   __syncthreads();
   const long long n_rows = min(*n_rows_p, cap);
@@ -256,6 +147,10 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
       dir0 = ddx * idist; dir1 = ddy * idist; dir2 = ddz * idist;
       X[32] = dir0; X[33] = dir1; X[34] = dir2;
       X[35] = in_dim == 36 ? dist : 0.f;
+      if (one_pass) {
+#pragma unroll
+        for (int j = 0; j < kMaxIn; ++j) X[j] = bf16r(X[j]);
+      }
 #pragma unroll
       for (int i = 0; i < kHidden; ++i) {
         const float4* w = reinterpret_cast<const float4*>(m.W1[i]);
@@ -266,7 +161,7 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
           acc = fmaf(ww.x, X[4 * q], acc); acc = fmaf(ww.y, X[4 * q + 1], acc);
           acc = fmaf(ww.z, X[4 * q + 2], acc); acc = fmaf(ww.w, X[4 * q + 3], acc);
         }
-        H[i] = fmaxf(acc, 0.f);
+        H[i] = one_pass ? bf16r(fmaxf(acc, 0.f)) : fmaxf(acc, 0.f);
       }
       // row scratch for the weight gradients, in 32-row blocks (sc_at)
 #pragma unroll
@@ -296,7 +191,7 @@ __global__ void __launch_bounds__(128) k_decode_bwd(const __grid_constant__ Batc
       any = true;
       float z[11];
 #pragma unroll
-      for (int t = 0; t < 11; ++t) z[t] = w2_dot(m, idx[t], H);
+      for (int t = 0; t < 11; ++t) z[t] = w2_dot(m, idx[t], H, round_colour && t >= 1 && t <= 3);
       const float op = sigm(z[0]);
       const float col[3] = {sigm(z[1]), sigm(z[2]), sigm(z[3])};
       const float sgs[3] = {sigm(z[4]), sigm(z[5]), sigm(z[6])};
@@ -424,7 +319,8 @@ __device__ __forceinline__ void wg_load(WgStage& v, const float* __restrict__ sc
 __global__ void __launch_bounds__(256) k_mlp_wgrad_partial(const float* __restrict__ sc_dZ, const float* __restrict__ sc_H,
                                                            const float* __restrict__ sc_dH, const float* __restrict__ sc_X,
                                                            const long long* __restrict__ n_rows_p, long long cap,
-                                                           int in_dim, float* __restrict__ partials) {
+                                                           int in_dim, int round_colour_h,
+                                                           float* __restrict__ partials) {
   __shared__ float sZ[kWgRows][kWgZ];
   __shared__ float sH[kWgRows][kWgH];
   __shared__ float sdH[kWgRows][kWgH];
@@ -441,6 +337,8 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad_partial(const float* __restri
   if (w2) { fa = (min(t, kWgTilesW2 - 1) / (kHidden / 4)) * 5; gb = (min(t, kWgTilesW2 - 1) % (kHidden / 4)) * 4; }
   else { const int u = t - kWgRole1; fa = (u / ((kMaxIn + 4) / 5)) * 4; gb = (u % ((kMaxIn + 4) / 5)) * 5; }
   const bool bias = gb == 0;          // also sums the bias entries of its rows
+  // dW2 tiles of colour outputs (rows 10..39, whole 5-row tiles) multiply BF16-rounded H in the BF16 form
+  const bool round_h = w2 && round_colour_h && fa >= kNOff && fa < 4 * kNOff;
   float acc[20], bs[5];
 #pragma unroll
   for (int i = 0; i < 20; ++i) acc[i] = 0.f;
@@ -469,7 +367,7 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad_partial(const float* __restri
 #pragma unroll
         for (int a = 0; a < 5; ++a) u[a] = sZ[rr][fa + a];
 #pragma unroll
-        for (int c = 0; c < 4; ++c) w[c] = sH[rr][gb + c];
+        for (int c = 0; c < 4; ++c) w[c] = round_h ? bf16r(sH[rr][gb + c]) : sH[rr][gb + c];
 #pragma unroll
         for (int a = 0; a < 5; ++a) {
           bs[a] += u[a];
@@ -552,10 +450,16 @@ __global__ void __launch_bounds__(256) k_mlp_wgrad_final(const float* __restrict
 
 int mlp_wgrad_outputs(int in_dim) { return wgrad_outputs(in_dim); }
 
+cudaError_t launch_mlp_wgrad_final(const float* partials, int nb, int in_dim, const pgs_param_grad_ptrs& out,
+                                   cudaStream_t st) {
+  k_mlp_wgrad_final<<<(wgrad_outputs(in_dim) + 31) / 32, 256, 0, st>>>(partials, nb, in_dim, out);
+  return cudaGetLastError();
+}
+
 void launch_mlp_wgrad(const float* dZ, const float* H, const float* dH, const float* X, const long long* n_rows,
-                      long long cap, int in_dim, float* partials, int nb, const pgs_param_grad_ptrs& out,
-                      cudaStream_t st) {
-  k_mlp_wgrad_partial<<<nb, 256, 0, st>>>(dZ, H, dH, X, n_rows, cap, in_dim, partials);
+                      long long cap, int in_dim, bool round_colour_h, float* partials, int nb,
+                      const pgs_param_grad_ptrs& out, cudaStream_t st) {
+  k_mlp_wgrad_partial<<<nb, 256, 0, st>>>(dZ, H, dH, X, n_rows, cap, in_dim, round_colour_h ? 1 : 0, partials);
   k_mlp_wgrad_final<<<(wgrad_outputs(in_dim) + 31) / 32, 256, 0, st>>>(partials, nb, in_dim, out);
 }
 

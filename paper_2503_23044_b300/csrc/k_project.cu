@@ -19,7 +19,7 @@ namespace pgs {
 __global__ void __launch_bounds__(256) k_project_explicit(const __grid_constant__ BatchDev b,
                                                           pgs_explicit_ptrs P, long long N, float4* __restrict__ rec,
                                                           uint32_t* __restrict__ counts,
-                                                          uint32_t* __restrict__ keys) {
+                                                          uint32_t* __restrict__ keys, uint32_t* err) {
   const long long G = N * b.n_views;
   for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < G;
        g += (long long)gridDim.x * blockDim.x) {
@@ -33,7 +33,7 @@ __global__ void __launch_bounds__(256) k_project_explicit(const __grid_constant_
     else { float iq = 1.f / qn; q[0] *= iq; q[1] *= iq; q[2] *= iq; q[3] *= iq; }
     float op = sigmoidf_(P.opacity_logits[i]);
     float col[3] = {P.colors[3 * i], P.colors[3 * i + 1], P.colors[3 * i + 2]};
-    project_gaussian(b, b.v[v], mu, s, q, op, col, rec + g * kRecF4, counts + g, keys + g);
+    project_gaussian(b, b.v[v], mu, s, q, op, col, rec + g * kRecF4, counts + g, keys + g, err);
   }
 }
 
@@ -118,7 +118,7 @@ __global__ void __launch_bounds__(256) k_decode_project(const __grid_constant__ 
                                                         pgs_mlp_ptrs Wt, const uint32_t* __restrict__ rows,
                                                         const long long* __restrict__ n_rows_p, long long cap,
                                                         float4* __restrict__ rec, uint32_t* __restrict__ counts,
-                                                        uint32_t* __restrict__ keys, DecodeOut dec) {
+                                                        uint32_t* __restrict__ keys, DecodeOut dec, uint32_t* err) {
   __shared__ MlpSmem m;
   const int in_dim = b.p.in_dim;
   load_mlp_smem(m, Wt, in_dim);
@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(256) k_decode_project(const __grid_constant__ 
         z[t] = acc;
       }
       const long long g = r * kNOff + j;
-      decode_gaussian(b, v, z, l, xa, A.offsets + (a * kNOff + j) * 3, g, rec, counts, keys, dec);
+      decode_gaussian(b, v, z, l, xa, A.offsets + (a * kNOff + j) * 3, g, rec, counts, keys, dec, err);
     }
   }
 }

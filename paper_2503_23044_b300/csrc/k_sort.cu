@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const long long* __restrict__ d_n, long long n_max, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
-    uint32_t* __restrict__ status_next, uint32_t* __restrict__ err, uint32_t spin_limit) {
+    uint32_t* __restrict__ status_next, uint32_t* __restrict__ err, uint32_t spin_limit, uint32_t hold_tile) {
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
   __shared__ uint32_t s_whist[kSortWarps][kRadix];
@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
       run += c;
     }
     uint32_t* st = status + tile * kRadix;
-    st_relaxed(st + d, (tile == 0 ? kStFlagInc : kStFlagAgg) | run);
+    // (hold_tile: a failure-path test hook; that tile never publishes, so the next one's wait runs out)
+    if (tile != hold_tile) st_relaxed(st + d, (tile == 0 ? kStFlagInc : kStFlagAgg) | run);
     unsigned long long tot;
     const uint32_t excl = (uint32_t)block_exclusive_scan_u64(run, s_w, tot);
     s_excl[d] = excl;
@@ -279,7 +280,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
         }
         j -= kLB;
       }
-      st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
+      if (tile != hold_tile) st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
     }
     s_gbase[d] = digit_off[d] + prefix - excl;
     if (status_next) status_next[tile * kRadix + d] = 0u;
@@ -319,9 +320,25 @@ __global__ void k_copy_pairs(const uint32_t* __restrict__ ks, const uint32_t* __
 
 int sort_passes(int bit_lo, int bit_hi) { return (bit_hi - bit_lo + 7) / 8; }
 
+// After a sort whose look-back wait ran out (kFlagTimeout set) the output may
+// hold stale entries; leave only indices the consumers can use safely:
+// identity values (vals[i] = i, i < n) or, without vals, no items (*d_n = 0).
+__global__ void k_sort_timeout_guard(const uint32_t* __restrict__ flags, long long* __restrict__ d_n, long long n_max,
+                                     uint32_t* __restrict__ vals) {
+  if (!(ld_relaxed(flags) & kFlagTimeout)) return;
+  if (!vals) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *d_n = 0;
+    return;
+  }
+  const long long n = max(0ll, min(*d_n, n_max));
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    vals[i] = (uint32_t)i;
+}
+
 cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                               const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
-                              uint32_t* err, uint32_t spin_limit, int num_sms, cudaStream_t st, int* n_launch) {
+                              uint32_t* err, uint32_t spin_limit, uint32_t hold_tile, int num_sms, cudaStream_t st,
+                              int* n_launch) {
   const int np = sort_passes(bit_lo, bit_hi);
   if (n_launch) *n_launch = 0;
   if (np <= 0) return cudaSuccess;
@@ -339,7 +356,8 @@ cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt
     k_sort_pass<<<pass_grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + 8 * p,
                                                      digit_mask(bit_lo + 8 * p, bit_hi), s.hist + p * kRadix,
                                                      s.counters + p, status[p & 1],
-                                                     p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit);
+                                                     p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit,
+                                                     hold_tile);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;

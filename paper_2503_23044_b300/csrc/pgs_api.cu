@@ -97,6 +97,21 @@ int resident_ctas_per_sm(const void* kernel, int threads, size_t smem, int carve
   return per_sm;
 }
 
+int prepare_smem_kernel(const void* kernel, int threads, size_t smem) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  const auto key = std::make_tuple(dev, kernel, threads, smem);
+  std::lock_guard<std::mutex> lk(launch_cache::mu);
+  auto it = launch_cache::occ.find(key);
+  if (it != launch_cache::occ.end()) return it->second;
+  cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  launch_cache::occ[key] = per_sm;
+  return per_sm;
+}
+
 int device_sm_count() {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return 1;
@@ -143,6 +158,7 @@ struct pgs_scene {
   BatchDev batch{};
   bool have_batch = false;
   uint32_t spin_limit = kDefaultSpinLimit;
+  uint32_t hold_tile = kNoHoldTile;   // failure-path test hook (pgs_scene_set_wait_limits)
   long long launches = 0;       // kernels enqueued since create
   bool prof = false;
   cudaEvent_t ev[PGS_N_STAGES][2] = {};
@@ -234,7 +250,8 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   if (p.n_levels < 1 || p.n_levels > 16) return fail(PGS_ERR_INVALID_ARG, "n_levels %d", p.n_levels);
   if (!(p.alpha_min > 0.f && p.alpha_min < p.alpha_max && p.alpha_max < 1.f && p.t_min > 0.f && p.near_plane > 0.f))
     return fail(PGS_ERR_INVALID_ARG, "render thresholds out of range");
-  if (p.decode_precision != PGS_DECODE_FP32 && p.decode_precision != PGS_DECODE_BF16)
+  if (p.decode_precision != PGS_DECODE_FP32 && p.decode_precision != PGS_DECODE_BF16 &&
+      p.decode_precision != PGS_DECODE_BF16_1PASS)
     return fail(PGS_ERR_INVALID_ARG, "decode_precision");
 
   pgs_scene* s = new pgs_scene();
@@ -344,6 +361,7 @@ pgs_status build_batch(pgs_scene* s, const pgs_camera* cams, int n_views, BatchD
   b.p.t_min = p.t_min; b.p.jclamp = p.jclamp; b.p.tile_pad = p.tile_pad; b.p.lod_d0 = p.lod_d0; b.p.bg = p.bg;
   b.p.n_levels = p.n_levels; b.p.tile_w = p.tile_w; b.p.tile_h = p.tile_h; b.p.in_dim = p.in_dim;
   b.p.blend_batch = p.blend_batch;
+  b.p.decode = p.decode_precision;
   b.n_views = n_views;
   long long pix = 0;
   long long tiles = 0;
@@ -394,7 +412,8 @@ pgs_status run_project(pgs_scene* s, const BatchDev& b, DecodeOut dec, bool proj
   if (s->d.mode == PGS_MODE_EXPLICIT) {
     const long long G = s->d.n_primitives * b.n_views;
     k_set_i64<<<1, 1, 0, st>>>(s->d_cnt + 1, G);
-    k_project_explicit<<<grid_for(G, 256, ns), 256, 0, st>>>(b, s->ex, s->d.n_primitives, s->rec, s->counts, s->keys_a);
+    k_project_explicit<<<grid_for(G, 256, ns), 256, 0, st>>>(b, s->ex, s->d.n_primitives, s->rec, s->counts, s->keys_a,
+                                                             s->d_flags);
     s->launches += 2;
   } else {
     const long long Na = s->d.n_primitives;
@@ -405,13 +424,13 @@ pgs_status run_project(pgs_scene* s, const BatchDev& b, DecodeOut dec, bool proj
     k_compact_rows<<<grid_for(tot, 256, ns), 256, 0, st>>>(s->cull_flags, s->cull_offs, tot, Na, s->rows, s->cap_rows,
                                                           s->d_flags);
     k_rows_total<<<1, 1, 0, st>>>(s->d_tot, s->cap_rows, s->d_cnt, s->d_cnt + 1, s->d_flags);
-    if (s->d.params.decode_precision == PGS_DECODE_BF16) {
-      const int grid = (int)std::max<long long>(1, std::min<long long>((s->cap_rows + 127) / 128, 2ll * ns));
-      k_decode_project_tc<<<grid, 384, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
-                                                project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags);
+    const int prec = s->d.params.decode_precision;
+    if (prec == PGS_DECODE_BF16 || prec == PGS_DECODE_BF16_1PASS) {
+      PGS_CUDA(launch_decode_project_tc(prec == PGS_DECODE_BF16, b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
+                                        project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags, st));
     } else {
       k_decode_project<<<ns * 4, 256, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
-                                              project ? s->rec : nullptr, s->counts, s->keys_a, dec);
+                                              project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags);
     }
     s->launches += 5 + kScanLaunches;
   }
@@ -460,8 +479,10 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
   prof_mark(s, PGS_STAGE_DEPTH_SORT, 0, st);
   k_iota<<<ns * 4, 256, 0, st>>>(s->gid_a, d_G);
   PGS_CUDA(launch_sort_pairs(s->keys_a, s->gid_a, s->keys_b, s->gid_b, d_G, s->cap_g, 0, 32, s->ss, s->d_flags,
-                             s->spin_limit, ns, st, &nl));
-  s->launches += 1 + nl;
+                             s->spin_limit, s->hold_tile, ns, st, &nl));
+  // a look-back wait that ran out leaves the order unspecified: fall back to index order (valid ids only)
+  k_sort_timeout_guard<<<ns * 2, 256, 0, st>>>(s->d_flags, s->d_cnt + 1, s->cap_g, s->gid_a);
+  s->launches += 2 + nl;
   prof_mark(s, PGS_STAGE_DEPTH_SORT, 1, st);
   // pair offsets in depth order, then emission
   prof_mark(s, PGS_STAGE_BIN, 0, st);
@@ -474,16 +495,18 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
   // stable sort of the pairs by tile, then per-tile ranges
   prof_mark(s, PGS_STAGE_TILE_SORT, 0, st);
   PGS_CUDA(launch_sort_pairs(s->ptile_a, s->pg_a, s->ptile_b, s->pg_b, d_P, s->cap_pairs, 0, tile_bits(b.total_tiles),
-                             s->ss, s->d_flags, s->spin_limit, ns, st, &nl));
+                             s->ss, s->d_flags, s->spin_limit, s->hold_tile, ns, st, &nl));
+  k_sort_timeout_guard<<<1, 32, 0, st>>>(s->d_flags, d_P, s->cap_pairs, nullptr);   // ran out: no pairs
   PGS_CUDA(cudaMemsetAsync(s->ranges, 0, (size_t)b.total_tiles * sizeof(uint2), st));
   k_tile_ranges<<<ns * 8, 256, 0, st>>>(s->ptile_a, d_P, s->ranges);
-  s->launches += nl + 1;
+  s->launches += nl + 2;
   // queue order for the persistent blend kernels: longest tile lists first
   k_set_i64<<<1, 1, 0, st>>>(s->d_cnt + 4, b.total_tiles);
   k_tile_order_keys<<<ns * 2, 256, 0, st>>>(s->ranges, b.total_tiles, s->order_k, s->order_v);
   PGS_CUDA(launch_sort_pairs(s->order_k, s->order_v, s->order_kb, s->order_vb, s->d_cnt + 4, s->max_tiles, 0, 24,
-                             s->ss, s->d_flags, s->spin_limit, ns, st, &nl));
-  s->launches += 2 + nl;
+                             s->ss, s->d_flags, s->spin_limit, s->hold_tile, ns, st, &nl));
+  k_sort_timeout_guard<<<ns, 256, 0, st>>>(s->d_flags, s->d_cnt + 4, s->max_tiles, s->order_v);  // ran out: tile order
+  s->launches += 3 + nl;
   prof_mark(s, PGS_STAGE_TILE_SORT, 1, st);
   prof_mark(s, PGS_STAGE_BLEND_FWD, 0, st);
   PGS_CUDA(cudaMemsetAsync(s->queue_ctr, 0, 2 * sizeof(uint32_t), st));
@@ -542,6 +565,17 @@ pgs_status pgs_backward(pgs_scene* s, const pgs_camera* cams, int n_views, const
                                                                      s->d_flags);
     s->launches += 1;
     prof_mark(s, PGS_STAGE_PROJECT_BWD, 1, st);
+  } else if (s->d.params.decode_precision == PGS_DECODE_BF16) {
+    // the tensor-core decoder's backward on the tensor cores
+    PGS_CUDA(launch_decode_bwd_tc(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows, s->grad_rec, *pg, s->sc_dZ,
+                                  s->sc_H, s->sc_dH, s->sc_X, s->d_flags, st));
+    s->launches += 1;
+    prof_mark(s, PGS_STAGE_PROJECT_BWD, 1, st);
+    prof_mark(s, PGS_STAGE_WGRAD, 0, st);
+    PGS_CUDA(launch_mlp_wgrad_tc(s->sc_dZ, s->sc_H, s->sc_dH, s->sc_X, s->d_cnt, s->cap_rows, s->d.params.in_dim,
+                                 s->wg_partials, s->wg_blocks, *pg, s->d_flags, st));
+    s->launches += 2;
+    prof_mark(s, PGS_STAGE_WGRAD, 1, st);
   } else {
     k_decode_bwd<<<ns * 4, 128, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows, s->grad_rec, *pg, s->sc_dZ,
                                         s->sc_H, s->sc_dH, s->sc_X, s->d_flags);
@@ -549,11 +583,18 @@ pgs_status pgs_backward(pgs_scene* s, const pgs_camera* cams, int n_views, const
     prof_mark(s, PGS_STAGE_PROJECT_BWD, 1, st);
     prof_mark(s, PGS_STAGE_WGRAD, 0, st);
     launch_mlp_wgrad(s->sc_dZ, s->sc_H, s->sc_dH, s->sc_X, s->d_cnt, s->cap_rows, s->d.params.in_dim,
-                     s->wg_partials, s->wg_blocks, *pg, st);
+                     s->d.params.decode_precision == PGS_DECODE_BF16, s->wg_partials, s->wg_blocks, *pg, st);
     s->launches += kWgradLaunches;
     prof_mark(s, PGS_STAGE_WGRAD, 1, st);
   }
   PGS_CUDA(cudaGetLastError());
+  return PGS_OK;
+}
+
+pgs_status pgs_scene_set_wait_limits(pgs_scene* s, uint32_t spin_limit, uint32_t withhold_tile) {
+  if (!s) return fail(PGS_ERR_INVALID_ARG, "null scene");
+  s->spin_limit = spin_limit ? spin_limit : kDefaultSpinLimit;
+  s->hold_tile = withhold_tile;
   return PGS_OK;
 }
 
@@ -825,7 +866,7 @@ pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_a
   if (scratch_bytes < ss.bytes) return fail(PGS_ERR_INVALID_ARG, "scratch %zu < %zu bytes", scratch_bytes, ss.bytes);
   const int ns = device_sm_count();
   PGS_CUDA(launch_sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, reinterpret_cast<const long long*>(d_n), n_max,
-                             bit_lo, bit_hi, ss, d_err ? d_err : ss.err, kDefaultSpinLimit, ns, stream));
+                             bit_lo, bit_hi, ss, d_err ? d_err : ss.err, kDefaultSpinLimit, kNoHoldTile, ns, stream));
   return PGS_OK;
 }
 

@@ -36,6 +36,7 @@ struct ViewDev {
 struct ParamsDev {
   float near_plane, dilation, alpha_min, alpha_max, t_min, jclamp, tile_pad, lod_d0, bg;
   int n_levels, tile_w, tile_h, in_dim, blend_batch;
+  int decode;          // pgs_decode_precision of the decoder forward (the backward follows its rounding)
 };
 
 struct BatchDev {
@@ -87,6 +88,51 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 __device__ __forceinline__ void set_flag(uint32_t* flags, uint32_t bit) { atomicOr(flags, bit); }
+
+// ---- packed FP32 pairs (sm_100 family): add / sub / mul / fma .rn.f32x2 round each half exactly as the
+// scalar __fadd_rn / __fsub_rn / __fmul_rn / __fmaf_rn would, at one issue slot for both halves
+struct f2 {
+  unsigned long long v;
+};
+__device__ __forceinline__ f2 f2_make(float lo, float hi) {
+  f2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ f2 f2_splat(float x) { return f2_make(x, x); }
+__device__ __forceinline__ float f2_lo(f2 a) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+  return lo;
+}
+__device__ __forceinline__ float f2_hi(f2 a) {
+  float lo, hi;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a.v));
+  return hi;
+}
+__device__ __forceinline__ f2 f2_add(f2 a, f2 b) {
+  f2 r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_sub(f2 a, f2 b) {
+  f2 r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+  return r;
+}
+__device__ __forceinline__ f2 f2_shfl_xor(f2 a, int m) {
+  return f2_make(__shfl_xor_sync(0xffffffffu, f2_lo(a), m), __shfl_xor_sync(0xffffffffu, f2_hi(a), m));
+}
 
 // ---- error-free transforms (Knuth TwoSum, FMA TwoProduct) for the 2D mean
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {

@@ -48,21 +48,27 @@ void set_last_error(const char* msg);
 int resident_ctas_per_sm(const void* kernel, int threads, size_t smem = 0, int carveout = -1);
 // pgs_api.cu: SM count of the current device (cached per device; thread-safe)
 int device_sm_count();
+// pgs_api.cu: allow `smem` bytes of dynamic shared memory for `kernel` on the current device (once per device)
+// and return its resident CTAs per SM at `threads` threads
+int prepare_smem_kernel(const void* kernel, int threads, size_t smem);
 
 // k_project.cu
 __global__ void k_project_explicit(const __grid_constant__ BatchDev b, pgs_explicit_ptrs P, long long N, float4* rec,
-                                   uint32_t* counts, uint32_t* keys);
+                                   uint32_t* counts, uint32_t* keys, uint32_t* err);
 __global__ void k_anchor_cull(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, long long Na, uint32_t* flags);
 __global__ void k_compact_rows(const uint32_t* flags, const uint32_t* offs, long long total, long long Na,
                                uint32_t* rows, long long cap, uint32_t* err);
 __global__ void k_decode_project(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, pgs_mlp_ptrs Wt,
                                  const uint32_t* rows, const long long* n_rows_p, long long cap, float4* rec,
-                                 uint32_t* counts, uint32_t* keys, DecodeOut dec);
+                                 uint32_t* counts, uint32_t* keys, DecodeOut dec, uint32_t* err);
 
-// k_decode_tc.cu
-__global__ void k_decode_project_tc(const __grid_constant__ BatchDev b, pgs_anchor_ptrs A, pgs_mlp_ptrs Wt,
-                                    const uint32_t* rows, const long long* n_rows_p, long long cap, float4* rec,
-                                    uint32_t* counts, uint32_t* keys, DecodeOut dec, uint32_t* err);
+// k_decode_tc.cu: the tensor-core decoder + projection; split = true is the production precision (layer 1 and
+// the opacity / scale / rotation heads FP32-accurate, colour heads one BF16 pass), false the one-pass study form
+size_t decode_tc_smem_bytes();
+cudaError_t launch_decode_project_tc(bool split, const BatchDev& b, const pgs_anchor_ptrs& A, const pgs_mlp_ptrs& W,
+                                     const uint32_t* rows, const long long* n_rows, long long cap, float4* rec,
+                                     uint32_t* counts, uint32_t* keys, const DecodeOut& dec, uint32_t* err,
+                                     cudaStream_t st);
 
 // k_sort.cu
 void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
@@ -75,10 +81,14 @@ constexpr size_t sort_scratch_bytes_for(long long n_max) {
 }
 SortScratch sort_scratch_layout(void* base, long long n_max);
 int sort_passes(int bit_lo, int bit_hi);
+// hold_tile: failure-path test hook (kNoHoldTile in production): that onesweep tile never publishes its
+// look-back status, so the next tile's bounded wait runs out and raises kFlagTimeout.
+constexpr uint32_t kNoHoldTile = 0xffffffffu;
 cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
                               const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
-                              uint32_t* err, uint32_t spin_limit, int num_sms, cudaStream_t st,
+                              uint32_t* err, uint32_t spin_limit, uint32_t hold_tile, int num_sms, cudaStream_t st,
                               int* n_launch = nullptr);
+__global__ void k_sort_timeout_guard(const uint32_t* flags, long long* d_n, long long n_max, uint32_t* vals);
 __global__ void k_emit_pairs(const __grid_constant__ BatchDev b, const float4* rec, const uint32_t* counts,
                              const uint32_t* sorted_g, const uint32_t* offs, const long long* d_ng, long long cap,
                              int mode, long long n_explicit, const uint32_t* rows, uint32_t* tiles_out,
@@ -133,8 +143,22 @@ __global__ void k_decode_bwd(const __grid_constant__ BatchDev b, pgs_anchor_ptrs
                              pgs_param_grad_ptrs out, float* sc_dZ, float* sc_H, float* sc_dH, float* sc_X,
                              uint32_t* err);
 int mlp_wgrad_outputs(int in_dim);
+// fixed-order sum of nb partial rows of the decoder weight gradients into out (accumulated)
+cudaError_t launch_mlp_wgrad_final(const float* partials, int nb, int in_dim, const pgs_param_grad_ptrs& out,
+                                   cudaStream_t st);
+// k_decode_bwd_tc.cu: the decoder weight gradients of PGS_DECODE_BF16 on the tensor cores from the row scratch
+// (at most nb_max partial rows)
+cudaError_t launch_mlp_wgrad_tc(const float* dZ, const float* H, const float* dH, const float* X,
+                                const long long* n_rows, long long cap, int in_dim, float* partials, int nb_max,
+                                const pgs_param_grad_ptrs& out, uint32_t* err, cudaStream_t st);
+// k_decode_bwd_tc.cu: the decoder backward of PGS_DECODE_BF16 on the tensor cores (fills the same row scratch)
+cudaError_t launch_decode_bwd_tc(const BatchDev& b, const pgs_anchor_ptrs& A, const pgs_mlp_ptrs& W,
+                                 const uint32_t* rows, const long long* n_rows, long long cap, const float* grad,
+                                 const pgs_param_grad_ptrs& out, float* sc_dZ, float* sc_H, float* sc_dH, float* sc_X,
+                                 uint32_t* err, cudaStream_t st);
+// round_colour_h: the colour rows of dW2 take BF16-rounded H (the one-pass colour heads of PGS_DECODE_BF16)
 void launch_mlp_wgrad(const float* dZ, const float* H, const float* dH, const float* X, const long long* n_rows,
-                      long long cap, int in_dim, float* partials, int nb, const pgs_param_grad_ptrs& out,
-                      cudaStream_t st);
+                      long long cap, int in_dim, bool round_colour_h, float* partials, int nb,
+                      const pgs_param_grad_ptrs& out, cudaStream_t st);
 
 }  // namespace pgs

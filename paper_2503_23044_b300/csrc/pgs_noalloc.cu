@@ -90,7 +90,7 @@ pgs_status pgs_sort_pairs_noalloc(uint32_t* d_keys, uint32_t* d_vals, int64_t n,
   k_noalloc_setup<<<1, 1, 0, stream>>>(d_n, (long long)n, own_err);
   const int ns = pgs::device_sm_count();
   e = pgs::launch_sort_pairs(d_keys, d_vals, alt_k, alt_v, d_n, kNoAllocMaxN, bit_lo, bit_hi, ss,
-                             d_err ? d_err : own_err, 1u << 20, ns, stream);
+                             d_err ? d_err : own_err, 1u << 20, pgs::kNoHoldTile, ns, stream);
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(g_msg, sizeof(g_msg), "pgs_sort_pairs_noalloc: launch: %s", cudaGetErrorString(e));

@@ -11,11 +11,18 @@ __device__ __forceinline__ float sigmoidf_(float x) { return 1.f / (1.f + expf(-
 // Project one 3D Gaussian into view v: writes the 64 B record, its tile count
 // and its depth key (0xffffffff when it touches no tile).  mu_lo (optional) is
 // the low part of a double-float mean: the camera-frame mean, hence the FP32
-// depth key and the 2D mean, come out correctly rounded.
+// depth key and the 2D mean, come out correctly rounded.  A non-finite mean,
+// scale, rotation, opacity or colour raises kFlagNonfinite in *err (if given);
+// such a Gaussian is never drawn.
 __device__ __forceinline__ void project_gaussian(const BatchDev& b, const ViewDev& v, const float mu[3], const float s[3],
                                  const float q[4], float opacity, const float col[3], float4* rec,
-                                 uint32_t* count_out, uint32_t* key_out, const float* mu_lo = nullptr) {
+                                 uint32_t* count_out, uint32_t* key_out, uint32_t* err,
+                                 const float* mu_lo = nullptr) {
   const ParamsDev& p = b.p;
+  if (err && !(isfinite(mu[0]) && isfinite(mu[1]) && isfinite(mu[2]) && isfinite(s[0]) && isfinite(s[1]) &&
+               isfinite(s[2]) && isfinite(q[0]) && isfinite(q[1]) && isfinite(q[2]) && isfinite(q[3]) &&
+               isfinite(opacity) && isfinite(col[0]) && isfinite(col[1]) && isfinite(col[2])))
+    set_flag(err, kFlagNonfinite);
   float xh, xl, yh, yl, zh, zl;
   float ex = 0.f, ey = 0.f, ez = 0.f;
   if (mu_lo) {
@@ -114,7 +121,8 @@ __device__ __forceinline__ float decoder_input(const pgs_anchor_ptrs& A, const V
 // (opacity, colour x3, scale x3, quaternion x4) before activation.
 __device__ __forceinline__ void decode_gaussian(const BatchDev& b, const ViewDev& v, const float z[11], const float l[3],
                                                 const float xa[3], const float* O, long long g, float4* rec,
-                                                uint32_t* counts, uint32_t* keys, const DecodeOut& dec) {
+                                                uint32_t* counts, uint32_t* keys, const DecodeOut& dec,
+                                                uint32_t* err) {
   const float op = sigmoidf_(z[0]);
   const float col[3] = {sigmoidf_(z[1]), sigmoidf_(z[2]), sigmoidf_(z[3])};
   const float s[3] = {l[0] * sigmoidf_(z[4]), l[1] * sigmoidf_(z[5]), l[2] * sigmoidf_(z[6])};
@@ -139,7 +147,7 @@ __device__ __forceinline__ void decode_gaussian(const BatchDev& b, const ViewDev
     dec.scale[3 * g] = s[0]; dec.scale[3 * g + 1] = s[1]; dec.scale[3 * g + 2] = s[2];
     dec.quat[4 * g] = q[0]; dec.quat[4 * g + 1] = q[1]; dec.quat[4 * g + 2] = q[2]; dec.quat[4 * g + 3] = q[3];
   }
-  if (rec) project_gaussian(b, v, mu, s, q, op, col, rec + g * kRecF4, counts + g, keys + g, mu_lo);
+  if (rec) project_gaussian(b, v, mu, s, q, op, col, rec + g * kRecF4, counts + g, keys + g, err, mu_lo);
 }
 
 }  // namespace pgs

@@ -1,6 +1,17 @@
-"""The decoder of Eq. 4 on the tensor cores (BF16 operands, FP32 accumulation):
-its outputs against the FP32 decoder, and BF16-decoded images against the
-FP64 oracle (exact decoder) with the stated bar: colour max-abs <= 5e-3."""
+"""The decoder of Eq. 4 on the tensor cores (BF16 operands, FP32 accumulation).
+
+PGS_DECODE_BF16 (the benchmarked form) takes the colour heads in one BF16
+pass and layer 1 plus the opacity, scale and rotation heads in an exact
+three-piece BF16 split; PGS_DECODE_BF16_1PASS (a precision study) rounds every
+operand once.  Checked here through the C ABI:
+
+- decoded Gaussians against the oracle's FP64 emulation of the same rounding
+  points (the tensor-core path computes the function it is meant to);
+- rendered images against that emulating oracle with the FP32 bars, and
+  against the exact FP64 oracle with the BF16 bar: max-abs <= 5e-3 on colour
+  and normal, 5e-3 relative on the unbiased depth, on unflagged pixels;
+- the one-pass form's image error against the exact oracle is stated (printed):
+  it is why the shape heads are split."""
 import numpy as np
 import pytest
 import torch
@@ -12,44 +23,119 @@ from tests.gpu_util import anchor_gpu, anchor_params, crop_view, image_errors
 
 pytestmark = pytest.mark.gpu
 
-TOL_BF16_RGB = 5e-3
+TOL_BF16 = 5e-3          # against the exact oracle: colour and normal max-abs, depth relative
+TOL_RGB = TOL_NORMAL = TOL_DEPTH_REL = 1e-4    # against the emulating oracle (the FP32 bars)
 
 
-def _decode(sc, precision):
+def _decode_gpu(sc, precision):
     scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=precision))
     out = scene.decode(sc["cameras"], capacity_rows=len(sc["x"]) * len(sc["cameras"]))
     scene.read_status()
-    return out
+    return {k: v.detach().cpu() for k, v in out.items()}
+
+
+def _decode_oracle(sc, rows, precision):
+    """The oracle's decoder for the GPU's (view, anchor) rows, in the given arithmetic."""
+    rows = rows.long()
+    lv = O.leaves_anchor(sc)
+    mlp = {k: lv[k].detach() for k in ("W1", "b1", "W2", "b2")}
+    anchors = {k: lv[k].detach() for k in ("x", "feat", "log_l", "offsets")}
+    out = {k: [] for k in ("opacity", "color", "scale", "quat")}
+    vs = (rows >> 27).numpy()
+    for v in sorted(set(vs.tolist())):
+        sel = np.nonzero(vs == v)[0]
+        idx = (rows[sel] & ((1 << 27) - 1))
+        d = O.decode(anchors, mlp, O.camera(sc["cameras"][v]), idx, 35, precision)
+        for k in out:
+            out[k].append((torch.as_tensor(sel), d[k].reshape(len(sel), 10, -1)))
+    res = {}
+    for k, parts in out.items():
+        w = parts[0][1].shape[-1]
+        full = torch.zeros(len(rows), 10, w, dtype=O.DT)
+        for sel, val in parts:
+            full[sel] = val
+        res[k] = full.reshape(len(rows) * 10, w).squeeze(-1)
+    return res
 
 
 @pytest.mark.parametrize("n_anchors", [300, 4000])
-def test_tensor_core_decoder_matches_fp32_decoder(n_anchors):
-    """Same rows, same Gaussian means (not decoded by the MLP); activations
-    within BF16 rounding of the FP32 decoder.  Covers a partial 128-row tile."""
+def test_tensor_core_decoder_matches_its_fp64_emulation(n_anchors):
+    """Same rows and means as the FP32 decoder.  Opacity, scale and rotation
+    (split heads) within 1e-5 of the oracle's emulation of the BF16 form and as
+    accurate as the FP32 decoder.  Colours (one BF16 pass over BF16-rounded H):
+    a hidden value computed to FP32 accuracy that sits within its rounding of a
+    BF16 midpoint may round to the other neighbour than the exact one, which
+    moves that row's colours by up to ~1e-3, so the colour bar is on the bulk
+    (median at FP32 level, at most 0.5% of values past 1e-5) plus that reach.
+    Covers a partial 128-row tile."""
     sc = synth.anchor_scene("anchor_1080p", n_anchors=n_anchors, resolutions=[(640, 360)])
-    a = _decode(sc, B.DECODE_FP32)
-    b = _decode(sc, B.DECODE_BF16)
+    a = _decode_gpu(sc, B.DECODE_FP32)
+    b = _decode_gpu(sc, B.DECODE_BF16)
     print("visible rows", len(a["rows"]))
     assert len(a["rows"]) > 0
-    assert torch.equal(a["rows"], b["rows"])
-    assert torch.equal(a["mu"], b["mu"])
-    for k, tol in (("opacity", 2e-2), ("color", 2e-2), ("scale", 2e-2), ("quat", 5e-2)):
-        d = (a[k] - b[k]).abs()
-        print(k, float(d.max()), float(d.mean()))
-        assert float(d.max()) <= tol * max(1.0, float(a[k].abs().max())), k
-        assert float(d.mean()) <= tol / 10 * max(1.0, float(a[k].abs().max())), k
+    assert torch.equal(a["rows"], b["rows"]) and torch.equal(a["mu"], b["mu"])
+    emu = _decode_oracle(sc, b["rows"], "bf16")
+    exact = _decode_oracle(sc, b["rows"], "fp64")
+    for k in ("opacity", "color", "scale", "quat"):
+        e = float((b[k].double().reshape(emu[k].shape) - emu[k]).abs().max())
+        x = float((b[k].double().reshape(exact[k].shape) - exact[k]).abs().max())
+        f = float((a[k].double().reshape(exact[k].shape) - exact[k]).abs().max())
+        print(f"{k:8s} BF16 vs its emulation {e:.2e} | BF16 vs exact {x:.2e} | FP32 vs exact {f:.2e}")
+        if k == "color":
+            d = (b[k].double().reshape(emu[k].shape) - emu[k]).abs().reshape(-1)
+            print(f"         colour median {float(d.median()):.2e}, fraction past 1e-5 {float((d > 1e-5).double().mean()):.2e}")
+            assert float(d.median()) <= 1e-6 and float((d > 1e-5).double().mean()) <= 5e-3 and e <= 2e-3
+        else:                                   # the split heads are as accurate as the FP32 decoder
+            assert e <= 1e-5, k
+            assert x <= max(4 * f, 2e-6), k
+
+
+def test_one_pass_decoder_matches_its_fp64_emulation():
+    """The study form rounds X, W1, H and W2 once.  An FP32-computed input or
+    hidden value that sits within its rounding of a BF16 midpoint may round
+    the other way than the FP64 emulation, which moves single outputs, so the
+    bar is on the bulk: the median error is at FP32 level and at most 0.5% of
+    the outputs differ by more than 1e-4."""
+    sc = synth.anchor_scene("anchor_1080p", n_anchors=4000, resolutions=[(640, 360)])
+    b = _decode_gpu(sc, B.DECODE_BF16_1PASS)
+    emu = _decode_oracle(sc, b["rows"], "bf16_1pass")
+    for k in ("opacity", "color", "scale", "quat"):
+        d = (b[k].double().reshape(emu[k].shape) - emu[k]).abs().reshape(-1)
+        print(f"{k:8s} median {float(d.median()):.2e} max {float(d.max()):.2e} "
+              f"frac>1e-4 {float((d > 1e-4).double().mean()):.2e}")
+        assert float(d.median()) <= 1e-6 and float((d > 1e-4).double().mean()) <= 5e-3, k
+
+
+def _images(sc, precision, crop=None, cap_rows=None):
+    scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=precision), cap_rows=cap_rows)
+    img = scene.render(sc["cameras"])
+    scene.read_status()
+    return img
+
+
+def _rp(sc, decode):
+    return O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]), decode=decode)
+
+
+def _check_bf16(gv, emu, exact):
+    e = image_errors(gv, emu, emu["flag"])
+    x = image_errors(gv, exact, exact["flag"])
+    print("  vs emulation", e)
+    print("  vs exact    ", x)
+    assert e["rgb"] <= TOL_RGB and e["normal"] <= TOL_NORMAL and e["depth_rel"] <= TOL_DEPTH_REL, e
+    assert e["n_contrib_mismatch"] == 0 and e["flagged"] < 0.01
+    assert x["rgb"] <= TOL_BF16 and x["normal"] <= TOL_BF16 and x["depth_rel"] <= TOL_BF16, x
+    assert x["flagged"] < 0.01
 
 
 def test_bf16_images_against_fp64_oracle_tiny():
     sc = synth.tiny_anchor_scene(n_anchors=6, seed=3, n_views=2, width=48, height=40)
-    orc = O.render(sc, O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"])))
-    scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=B.DECODE_BF16))
-    img = scene.render(sc["cameras"])
-    scene.read_status()
+    img = _images(sc, B.DECODE_BF16)
+    emu = O.render(sc, _rp(sc, "bf16"))
+    exact = O.render(sc, _rp(sc, "fp64"))
     for v in range(2):
-        e = image_errors(img.view(v), orc["views"][v], orc["views"][v]["flag"])
-        print("bf16 tiny view", v, e)
-        assert e["rgb"] <= TOL_BF16_RGB
+        print("bf16 tiny view", v)
+        _check_bf16(img.view(v), emu["views"][v], exact["views"][v])
 
 
 @pytest.mark.parametrize("seed", [1, 2])
@@ -58,11 +144,60 @@ def test_bf16_images_against_fp64_oracle_1080p_crop(seed):
     cam = sc["cameras"][0]
     rng = np.random.default_rng(seed)
     crop = (int(rng.integers(0, cam.width - 64)), int(rng.integers(cam.height // 3, cam.height - 64)), 64, 64)
-    rp = O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))
-    orc = O.render(sc, rp, crops=[crop])["views"][0]
-    scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=B.DECODE_BF16), cap_rows=len(sc["x"]))
-    img = scene.render([cam])
+    img = _images(sc, B.DECODE_BF16, cap_rows=len(sc["x"]))
+    emu = O.render(sc, _rp(sc, "bf16"), crops=[crop])["views"][0]
+    exact = O.render(sc, _rp(sc, "fp64"), crops=[crop])["views"][0]
+    print("bf16 1080p crop", crop)
+    _check_bf16(crop_view(img.view(0), crop), emu, exact)
+
+
+def test_one_pass_bf16_image_error_is_stated():
+    """The study form's error against the exact oracle on a 1080p crop:
+    colour stays near 1e-3, the normal and depth do not (the quaternion
+    normalisation and the smallest-scale argmin amplify the rounding).
+    Printed, with only a sanity bound."""
+    sc = synth.anchor_scene("anchor_1080p")
+    cam = sc["cameras"][0]
+    crop = (900, 700, 64, 64)
+    img = _images(sc, B.DECODE_BF16_1PASS, cap_rows=len(sc["x"]))
+    exact = O.render(sc, _rp(sc, "fp64"), crops=[crop])["views"][0]
+    x = image_errors(crop_view(img.view(0), crop), exact, exact["flag"])
+    print("one-pass BF16 vs exact", x)
+    assert x["rgb"] < 5e-2 and np.isfinite(x["normal"]) and np.isfinite(x["depth_rel"])
+
+
+@pytest.mark.parametrize("case", ["tiny", "1080p_crop"])
+def test_bf16_backward_on_the_tensor_cores_matches_the_emulating_oracle(case):
+    """The BF16 form's backward (projection backward per Gaussian, then dH =
+    dZ W2, dX = dH' W1 and the weight-gradient reduction on the tensor cores)
+    against the autograd gradient of the oracle that emulates the forward's
+    rounding, rel-L2 <= 1e-3 on every anchor and decoder tensor."""
+    from tests.gpu_util import rel_l2
+    if case == "tiny":
+        sc = synth.tiny_anchor_scene(n_anchors=6, seed=3, n_views=2, width=48, height=40)
+        crops, cap_rows = None, None
+    else:
+        sc = synth.anchor_scene("anchor_1080p")
+        crops, cap_rows = [(900, 700, 64, 64)], len(sc["x"])
+    cams = sc["cameras"]
+    rp = _rp(sc, "bf16")
+    orc0 = O.render(sc, rp, crops=crops)
+    grads = synth.random_image_grads(cams, seed=13, scale=1e-2, crops=crops)
+    for v, gv in enumerate(grads):
+        ok = torch.zeros(cams[v].height, cams[v].width, dtype=torch.bool)
+        x0, y0, w, h = crops[v] if crops else (0, 0, cams[v].width, cams[v].height)
+        ok[y0:y0 + h, x0:x0 + w] = ~orc0["views"][v]["flag"]
+        grads[v] = {k: g * ok.float() for k, g in gv.items()}
+    leaves = O.leaves_anchor(sc)
+    O.render(sc, rp, leaves=leaves, crops=crops,
+             image_grads=[{k: (g[..., y0:y0 + hh, x0:x0 + ww] if crops else g) for k, g in gv.items()}
+                          for gv, (x0, y0, ww, hh) in zip(grads, crops or [(0, 0, c.width, c.height) for c in cams])])
+    scene, t = anchor_gpu(sc, params=anchor_params(sc, decode_precision=B.DECODE_BF16), cap_rows=cap_rows)
+    img = scene.render(cams)
+    pg = {k: torch.zeros_like(x, dtype=torch.float32) for k, x in t.items() if k != "level"}
+    scene.backward(cams, img, B.ImageGrads.from_views(grads), pg)
     scene.read_status()
-    e = image_errors(crop_view(img.view(0), crop), orc, orc["flag"])
-    print("bf16 1080p crop", crop, e)
-    assert e["rgb"] <= TOL_BF16_RGB
+    for k in pg:
+        e = rel_l2(pg[k], leaves[k].grad)
+        print(case, k, f"{e:.2e}")
+        assert e <= 1e-3, (k, e)

@@ -1,11 +1,20 @@
 """The two large configurations on one GPU against the FP64 oracle on 64x64
 crops: the 4K precision variant (4 views of 3840x2160 over 500k anchors, 5M
 neural Gaussians) with the BF16 tensor-core decoder and with the FP32 decoder,
-and the uneven street batch (16 views at four resolutions over 1M anchors,
-10M neural Gaussians).  Each case renders the whole batch in one call, then
-compares images on one crop per view (street: one per resolution class) and
-the parameter gradients of a seeded image-space gradient placed on those
-crops (unflagged pixels only)."""
+the benchmark's 8-view 1600x1064 batch in both precisions, and the uneven
+street batch (16 views at four resolutions over 1M anchors, 10M neural
+Gaussians).  Each case renders the whole batch in one call, then compares
+images on one crop per view (street: one per resolution class) and the
+parameter gradients of a seeded image-space gradient placed on those crops
+(unflagged pixels only).
+
+The BF16 decoder is compared twice: against the oracle that emulates its
+rounding (the colour heads' one BF16 pass; everything else exact), with the
+FP32 bars of images and gradients, and against the exact FP64 oracle with the
+BF16 image bar max-abs <= 5e-3 on colour and normal and 5e-3 relative on the
+unbiased depth, on every unflagged pixel.  Its gradient error against the
+exact oracle is stated (printed), not bounded: the colour heads' rounding is
+part of the function whose gradient is taken."""
 import numpy as np
 import pytest
 import torch
@@ -21,14 +30,7 @@ TOL_RGB = 1e-4            # FP32 decoder: the FP32 image bar
 TOL_DEPTH_REL = 1e-4
 TOL_NORMAL = 1e-4
 TOL_GRAD = 1e-3
-TOL_BF16_RGB = 5e-3       # BF16 decoder: image bar
-# BF16 decoder, gradients: a stated bound, not a paper bar.  The rounded decode
-# moves opacities enough to shift where about a tenth of the crop pixels stop
-# (T < t_min), so the contributor sets differ from the exact model's and the
-# position gradients, which sum over every contributor, move most (measured
-# rel-L2: 4e-2 .. 1.1e-1 on the 8-view batch, 1.3e-2 .. 2.2e-2 at 4K).  The
-# FP32 decoder meets TOL_GRAD on the same crops.
-TOL_BF16_GRAD = 0.25
+TOL_BF16 = 5e-3           # BF16 decoder against the exact oracle: colour and normal max-abs, depth relative
 MAX_FLAGGED = 0.03        # per crop (pixels the oracle marks as within rounding of a threshold)
 MAX_FLAGGED_MEAN = 0.01   # mean over a configuration's crops
 
@@ -53,13 +55,17 @@ def _lower_crops(sc, rp, views, seed, size=64, tries=8):
     return out
 
 
-def _rp(sc):
-    return O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]))   # the scene's LoD rule
+def _rp(sc, decode="fp64"):
+    return O.RenderParams(lod_d0=float(sc["lod_d0"]), n_levels=int(sc["n_levels"]), decode=decode)   # the scene's LoD rule
 
 
 def _run(sc, precision, views, crops, seed, **launch):
+    """Oracle in the GPU decoder's arithmetic (FP64, or FP64 emulating the
+    BF16 decoder's rounding) against the GPU: images on the crops, gradients
+    of a crop-restricted image gradient.  For the BF16 decoder also the image
+    errors against the exact FP64 oracle (key 'exact')."""
     cams = sc["cameras"]
-    rp = _rp(sc)
+    rp = _rp(sc, "bf16" if precision == B.DECODE_BF16 else "fp64")
     leaves = O.leaves_anchor(sc)
     all_crops = [crops.get(v) for v in range(len(cams))]
     og = {}
@@ -85,15 +91,41 @@ def _run(sc, precision, views, crops, seed, **launch):
     img = scene.render(cams)
     scene.read_status()
     errs = {}
+    exact = O.render(sc, _rp(sc), crops=all_crops, views=views) if precision == B.DECODE_BF16 else None
     for i, v in enumerate(views):
         ov = orc0["views"][i]
         print(f"  view {v}: anchors within 1e-5 of a LoD threshold: {int(ov['lod_amb'].sum())}")
         errs[v] = image_errors(crop_view(img.view(v), crops[v]), ov, ov["flag"])
+        if exact is not None:
+            ev = exact["views"][i]
+            errs[v]["exact"] = image_errors(crop_view(img.view(v), crops[v]), ev, ev["flag"])
     pg = {k: torch.zeros_like(x, dtype=torch.float32) for k, x in t.items() if k != "level"}
     scene.backward(cams, img, B.ImageGrads.from_views(full), pg)
     scene.read_status()
     gerr = {k: rel_l2(pg[k], leaves[k].grad) for k in pg}
+    if precision == B.DECODE_BF16:            # stated: the BF16 form's gradients against the exact model's
+        lx = O.leaves_anchor(sc)
+        O.render(sc, _rp(sc), leaves=lx, crops=all_crops, image_grads=cgr, views=views)
+        print("  BF16 gradient rel-L2 against the exact FP64 oracle:",
+              {k: f"{rel_l2(pg[k], lx[k].grad):.2e}" for k in pg})
     return errs, gerr, scene.stats()
+
+
+def _check(errs, gerr, views):
+    """The FP32 bars against the oracle in the decoder's own arithmetic and,
+    for the BF16 decoder, the 5e-3 bar against the exact oracle."""
+    for v in views:
+        e = errs[v]
+        assert e["flagged"] < MAX_FLAGGED
+        assert e["rgb"] <= TOL_RGB and e["depth_rel"] <= TOL_DEPTH_REL and e["normal"] <= TOL_NORMAL, (v, e)
+        assert e["n_contrib_mismatch"] == 0
+        if "exact" in e:
+            x = e["exact"]
+            assert x["flagged"] < MAX_FLAGGED
+            assert x["rgb"] <= TOL_BF16 and x["normal"] <= TOL_BF16 and x["depth_rel"] <= TOL_BF16, (v, x)
+    assert np.mean([errs[v]["flagged"] for v in views]) < MAX_FLAGGED_MEAN
+    for k, e in gerr.items():
+        assert e <= TOL_GRAD, (k, e)
 
 
 @pytest.mark.parametrize("precision", [B.DECODE_FP32, B.DECODE_BF16])
@@ -108,21 +140,8 @@ def test_batch8_1600_training_batch_on_a_crop_of_each_view(precision):
     print(f"batch8 {name}: pairs {st.pairs} gaussian-views {st.gaussian_views}")
     for v in views:
         print(f"  view {v} crop {crops[v]}: {errs[v]}")
-        assert errs[v]["flagged"] < MAX_FLAGGED
-    assert np.mean([errs[v]["flagged"] for v in views]) < MAX_FLAGGED_MEAN
     print("  gradient rel-L2:", {k: f"{e:.2e}" for k, e in gerr.items()})
-    if precision == B.DECODE_FP32:
-        for v in views:
-            e = errs[v]
-            assert e["rgb"] <= TOL_RGB and e["depth_rel"] <= TOL_DEPTH_REL and e["normal"] <= TOL_NORMAL, (v, e)
-            assert e["n_contrib_mismatch"] == 0
-        for k, e in gerr.items():
-            assert e <= TOL_GRAD, (k, e)
-    else:
-        for v in views:
-            assert errs[v]["rgb"] <= TOL_BF16_RGB, (v, errs[v])
-        for k, e in gerr.items():
-            assert e <= TOL_BF16_GRAD, (k, e)
+    _check(errs, gerr, views)
 
 
 @pytest.fixture(scope="module")
@@ -140,21 +159,8 @@ def test_4k_precision_variant_on_a_crop_of_each_view(scene_4k, precision):
     print(f"4K {name}: pairs {st.pairs} gaussian-views {st.gaussian_views}")
     for v in views:
         print(f"  view {v} crop {crops[v]}: {errs[v]}")
-        assert errs[v]["flagged"] < MAX_FLAGGED
-    assert np.mean([errs[v]["flagged"] for v in views]) < MAX_FLAGGED_MEAN
     print("  gradient rel-L2:", {k: f"{e:.2e}" for k, e in gerr.items()})
-    if precision == B.DECODE_FP32:
-        for v in views:
-            e = errs[v]
-            assert e["rgb"] <= TOL_RGB and e["depth_rel"] <= TOL_DEPTH_REL and e["normal"] <= TOL_NORMAL, (v, e)
-            assert e["n_contrib_mismatch"] == 0
-        for k, e in gerr.items():
-            assert e <= TOL_GRAD, (k, e)
-    else:
-        for v in views:   # colour bar; the normal is the smallest decoded scale's axis and may swap
-            assert errs[v]["rgb"] <= TOL_BF16_RGB, (v, errs[v])
-        for k, e in gerr.items():
-            assert e <= TOL_BF16_GRAD, (k, e)
+    _check(errs, gerr, views)
 
 
 def test_street_uneven_batch_on_a_crop_per_resolution():
@@ -165,11 +171,6 @@ def test_street_uneven_batch_on_a_crop_per_resolution():
     errs, gerr, st = _run(sc, B.DECODE_FP32, views, crops, seed=90)
     print(f"street: pairs {st.pairs} gaussian-views {st.gaussian_views} rows {st.rows}")
     for v in views:
-        e = errs[v]
-        print(f"  view {v} ({cams[v].width}x{cams[v].height}) crop {crops[v]}: {e}")
-        assert e["flagged"] < MAX_FLAGGED
-        assert e["rgb"] <= TOL_RGB and e["depth_rel"] <= TOL_DEPTH_REL and e["normal"] <= TOL_NORMAL, (v, e)
-        assert e["n_contrib_mismatch"] == 0
+        print(f"  view {v} ({cams[v].width}x{cams[v].height}) crop {crops[v]}: {errs[v]}")
     print("  gradient rel-L2:", {k: f"{e:.2e}" for k, e in gerr.items()})
-    for k, e in gerr.items():
-        assert e <= TOL_GRAD, (k, e)
+    _check(errs, gerr, views)
