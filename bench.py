@@ -41,6 +41,8 @@ FP32_LANES_PER_SM = 128
 # 13 per-pair gradients).
 FWD_FLOPS_EVAL, FWD_FLOPS_CONTRIB = 12, 18
 BWD_FLOPS_EVAL, BWD_FLOPS_CONTRIB = 12, 70
+# the coarser op model the scope table states: ~30 FP32 ops per evaluation forward, ~70 backward
+FWD_FLOPS_8D, BWD_FLOPS_8D = 30, 70
 
 
 def _peaks():
@@ -233,11 +235,19 @@ def run_reference(args):
     sc["sparse"] = synth.sparse_points(sc["terrain"], sc["extent"], N_SPARSE, seed=0)
     t_prior = cpu_prior_seconds(sc, pseudo)
     t_ncc = cpu_ncc_seconds(sc, marched)
-    per_step = []
+    full, ran, crop_px, frame_px = [], [], 0, 0
     for s in range(args.warmup + args.steps):
-        vps, _ = cpu_views_per_s(sc, None, [s % V])
-        per_step.append(1.0 / vps + (t_prior + t_ncc) / V)
-    timed = per_step[args.warmup:]
+        v = s % V
+        ts, tc, npx = cpu_oracle_sample(sc, None, v)
+        cam = sc["cameras"][v]
+        scale = cam.width * cam.height / npx
+        # measured: the view's setup and one crop; extrapolated: the crop's per-pixel cost over the frame
+        ran.append(ts + tc)
+        full.append(ts + tc * scale + (t_prior + t_ncc) / V)
+        if s >= args.warmup:
+            crop_px += npx
+            frame_px += cam.width * cam.height
+    timed, timed_ran = full[args.warmup:], ran[args.warmup:]
     value = len(timed) / sum(timed)
     cores = torch.get_num_threads()
     sample = (f"per step one of the {V} views ({resolution_desc(sc['cameras'])}): FP64 decode+projection of every "
@@ -245,9 +255,21 @@ def run_reference(args):
               f"{CPU_CROP}x{CPU_CROP} crop fwd+bwd; per-pixel cost extrapolated to the full frame; plus 1/{V} of the "
               f"batch's FP64 enhanced depth-prior filter ({t_prior:.2f} s for all views, timed once) and of its FP64 "
               f"NCC loss + gradients ({NCC_SAMPLE} patches per pair timed once, scaled to {N_PATCH}: {t_ncc:.2f} s)")
+    # ms_per_step is what each step actually ran (one view's decode + projection and one crop fwd+bwd);
+    # value is the full-view rate those samples extrapolate to (see "extrapolation")
     line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=args.gpus, steps=args.steps, warmup=args.warmup,
-                ms_per_step=1e3 * sum(timed) / len(timed), higher_is_better=True, scaling="weak", vs_baseline=None,
-                dtype="f64", data="synthetic", impl="reference",
+                ms_per_step=1e3 * sum(timed_ran) / len(timed_ran), higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f64", data="synthetic", impl="reference",
+                extrapolation=dict(what="value is extrapolated: per step one view's decode+projection and one "
+                                        f"{CPU_CROP}x{CPU_CROP} crop fwd+bwd were run; the crop's per-pixel cost is "
+                                        "scaled to the full frame and 1/V of the batch's prior filter and NCC (each "
+                                        "timed once) is added",
+                                   measured_s_per_step=sum(timed_ran) / len(timed_ran),
+                                   extrapolated_s_per_full_view=sum(timed) / len(timed),
+                                   crop_pixels_per_step=crop_px // max(1, len(timed)),
+                                   frame_pixels_per_step=frame_px // max(1, len(timed)),
+                                   pixel_scale=frame_px / max(1, crop_px),
+                                   prior_s_all_views=t_prior, ncc_s_all_views_scaled=t_ncc),
                 config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
                             resolution=resolution_desc(sc["cameras"]), l2="n/a (CPU)"),
                 cpu_baseline=dict(value=value, unit="views/s", cores=cores, kind="oracle", sample=sample),
@@ -407,7 +429,7 @@ def run_pgs(args):
     scene.set_profiling(False)
 
     # plain form: one view per call sequence, eager, no graph, FP32 decoder
-    plain_vps = None
+    plain_vps, plain_stage, plain_counts = None, None, None
     if not args.no_plain:
         pscene, _, _ = build_scene(sc, B, device, 1 << 26, len(sc["x"]), B.DECODE_FP32)
         pscene.bind_anchors(t["x"], t["level"], t["log_l"], t["offsets"], t["feat"], t["W1"], t["b1"], t["W2"], t["b2"])
@@ -457,6 +479,30 @@ def run_pgs(args):
             pm += e0.elapsed_time(e1)
         pscene.read_status(stream)
         plain_vps = job_rate(V * ks, world, max_over_ranks(pm, dist, device))
+        # one more plain step with the stage events on, read view by view (outside the timed region):
+        # per-stage time of the plain step and the pixel-Gaussian counts of its own renders
+        pscene.set_profiling(True)
+        plain_stage = {k: 0.0 for k in B.STAGES}
+        with torch.cuda.stream(stream):
+            pscene.filter_depth_prior(cams, pseudo, sparse, tau_d=1.0, k_neighbors=2, packed=packed, out=pprior)
+        for k, v in pscene.stage_times().items():
+            plain_stage[k] += max(v, 0.0)
+        for i, c in enumerate(cams):
+            with torch.cuda.stream(stream):
+                pscene.render([c], pimgs[i], packed=pk[i])
+                pscene.loss_grad([c], pimgs[i], ptg[i], loss=loss, grads=pgr[i], packed=pk[i])
+                if i % 2 == 1:
+                    q = i // 2
+                    pscene.ncc_loss_grad(cams[i - 1:i + 1], ppairs[q][0], centers[q:q + 1], ppairs[q][1],
+                                         lambda_ncc=LAMBDA_NCC, ncc_out=pncc[q * N_PATCH:(q + 1) * N_PATCH],
+                                         loss=ncc_loss, packed=pkp[q])
+                pscene.backward([c], pimgs[i], pgr[i], pg, packed=pk[i])
+            for k, v in pscene.stage_times().items():
+                if k != "prior":
+                    plain_stage[k] += max(v, 0.0)
+        pscene.set_profiling(False)
+        pscene.read_status(stream)
+        plain_counts = dict(n_eval=float(pimg_all.n_eval.double().sum()), n_contrib=float(pimg_all.n_contrib.double().sum()))
         pscene.close()
 
     # end to end through the public API: every step's inputs (target colour, pseudo depth)
@@ -552,28 +598,44 @@ def run_pgs(args):
                     volume="400x400x200 voxels of 0.01, truncation 0.04, rendered depth and colour of the batch")
         del vol
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel (batched form, and the plain form's own)
     peaks = _peaks()
-    dom = max(("blend_bwd", "blend_fwd", "tile_sort", "depth_sort", "project", "project_bwd", "wgrad", "bin", "loss",
-               "prior", "ncc"),
-              key=lambda k: stage_ms.get(k, 0.0))
     sm_count = torch.cuda.get_device_properties(local).multi_processor_count
-    fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+    clocks = clk.summary()
     P = int(stats.pairs)
-    if dom in ("blend_bwd", "blend_fwd"):
-        fl = (BWD_FLOPS_EVAL * n_eval + BWD_FLOPS_CONTRIB * n_contrib) if dom == "blend_bwd" else \
-             (FWD_FLOPS_EVAL * n_eval + FWD_FLOPS_CONTRIB * n_contrib)
-        ach = fl / (stage_ms[dom] / 1e3) / 1e12
-        roof = dict(bound="alu", kernel=f"k_{dom}", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
-                    traffic=MEASURED_TRAFFIC.get((args.workload, dom)), flops_per_launch=fl, peak_src=f"{sm_count} SMs x 128 FP32 lanes x 2 x "
-                    f"{peaks['sm_max_mhz']:.0f} MHz")
-    else:
-        nb = {"tile_sort": 2 * 16 * P * math.ceil(max(1, math.log2(max(2, stats.tiles))) / 8) + 4 * P,
-              "depth_sort": 4 * 16 * stats.gaussian_views + 4 * stats.gaussian_views}.get(dom, 64 * stats.gaussian_views)
-        ach = nb / (stage_ms[dom] / 1e3) / 1e9
-        roof = dict(bound="hbm", kernel=dom, achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
-                    frac=ach / peaks["hbm_gbs"], traffic=None, bytes_per_launch=nb)
-    roof["peak_source"] = peaks["src"]
+
+    def roofline(stages, ne, nc, traffic_ok):
+        dom = max(("blend_bwd", "blend_fwd", "tile_sort", "depth_sort", "project", "project_bwd", "wgrad", "bin",
+                   "loss", "prior", "ncc"), key=lambda k: stages.get(k, 0.0))
+        fp32_peak = sm_count * FP32_LANES_PER_SM * 2 * peaks["sm_max_mhz"] * 1e6 / 1e12
+        if dom in ("blend_bwd", "blend_fwd"):
+            bwd = dom == "blend_bwd"
+            fl = (BWD_FLOPS_EVAL * ne + BWD_FLOPS_CONTRIB * nc) if bwd else (FWD_FLOPS_EVAL * ne + FWD_FLOPS_CONTRIB * nc)
+            fl8 = (BWD_FLOPS_8D if bwd else FWD_FLOPS_8D) * ne
+            sec = stages[dom] / 1e3
+            ach, ach8 = fl / sec / 1e12, fl8 / sec / 1e12
+            r = dict(bound="alu", kernel=f"k_{dom}", achieved=ach, peak=fp32_peak, unit="TFLOP/s", frac=ach / fp32_peak,
+                     traffic=MEASURED_TRAFFIC.get((args.workload, dom)) if traffic_ok else None,
+                     flops_per_launch=fl, ms=stages[dom],
+                     op_model=f"{BWD_FLOPS_EVAL if bwd else FWD_FLOPS_EVAL} flops per evaluation + "
+                              f"{BWD_FLOPS_CONTRIB if bwd else FWD_FLOPS_CONTRIB} per contribution",
+                     achieved_scope_model=ach8, frac_scope_model=ach8 / fp32_peak,
+                     scope_model=f"{BWD_FLOPS_8D if bwd else FWD_FLOPS_8D} flops per pixel-Gaussian evaluation",
+                     peak_src=f"{sm_count} SMs x 128 FP32 lanes x 2 x {peaks['sm_max_mhz']:.0f} MHz")
+            if clocks.get("sm_mhz"):
+                r["frac_at_median_clock"] = r["frac"] * peaks["sm_max_mhz"] / clocks["sm_mhz"]
+                r["frac_scope_model_at_median_clock"] = r["frac_scope_model"] * peaks["sm_max_mhz"] / clocks["sm_mhz"]
+        else:
+            nb = {"tile_sort": 2 * 16 * P * math.ceil(max(1, math.log2(max(2, stats.tiles))) / 8) + 4 * P,
+                  "depth_sort": 4 * 16 * stats.gaussian_views + 4 * stats.gaussian_views}.get(dom, 64 * stats.gaussian_views)
+            ach = nb / (stages[dom] / 1e3) / 1e9
+            r = dict(bound="hbm", kernel=dom, achieved=ach, peak=peaks["hbm_gbs"], unit="GB/s",
+                     frac=ach / peaks["hbm_gbs"], traffic=None, bytes_per_launch=nb, ms=stages[dom])
+        r["peak_source"] = peaks["src"]
+        return r
+
+    roof = roofline(stage_ms, n_eval, n_contrib, True)
+    plain_roof = roofline(plain_stage, plain_counts["n_eval"], plain_counts["n_contrib"], False) if plain_stage else None
 
     # CPU oracle baseline on a bounded sample (rank 0, N = 1 only)
     cpu = None
@@ -591,14 +653,14 @@ def run_pgs(args):
                    seconds=dict(prior=t_prior, ncc_scaled=t_ncc, setup=sum(p[0] for p in parts),
                                 crops=sum(p[1] for p in parts)))
 
-    clocks = clk.summary()
     if rank == 0:
         line = dict(metric=METRIC, value=value, unit="views/s", n_gpus=world, steps=args.steps, warmup=args.warmup,
                     ms_per_step=ms_per_step, higher_is_better=True, scaling="weak", vs_baseline=None, dtype="f32",
                     data="synthetic",
                     config=dict(workload=args.workload, views=V, anchors=len(sc["x"]), gaussians=10 * len(sc["x"]),
                                 resolution=res_desc, form="batched: all views per call, CUDA graph" if use_graph
-                                else "batched: all views per call, eager", decode="BF16 tcgen05 (FP32 accumulate)" if args.decode == "bf16" else "FP32 SIMT",
+                                else "batched: all views per call, eager", decode="BF16 tcgen05, FP32 accumulate (colour heads one pass; layer 1, opacity, scale, rotation "
+                                                          "three-piece split)" if args.decode == "bf16" else "FP32 SIMT",
                                 tile=tile_desc, blend_batch=tp["blend_batch"],
                                 autotune=[f"{e['tile_w']}x{e['tile_h']}/{e['blend_batch']}: {e['ms']:.3f} ms" for e in tune]
                                 if tune else "off",
@@ -609,7 +671,8 @@ def run_pgs(args):
                                 l2="flushed between timed steps (256 MB write)",
                                 parallelism=f"replicas x{world}"),
                     plain=dict(value=plain_vps, unit="views/s", form="batch depth-prior filter, then one view per call "
-                                                                       "sequence, eager, FP32 decoder"),
+                                                                       "sequence, eager, FP32 decoder",
+                               roofline=plain_roof, stage_ms=plain_stage),
                     e2e=dict(value=e2e_vps, unit="views/s", h2d_bytes_per_step=h2d, d2h_bytes_per_step=d2h,
                              steps=ke, form="inputs copied from pinned host memory on a copy stream, one step "
                                          "ahead (two input sets, two graphs); losses read back every step"),

@@ -53,7 +53,8 @@ enum pgs_status_code {
   PGS_ERR_TIMEOUT = 3,       /* a bounded device-side wait (sort look-back) ran out */
   PGS_ERR_NONFINITE = 4,     /* non-finite value met in a parameter, a loss or a gradient */
   PGS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
-  PGS_ERR_UNSUPPORTED = 6    /* valid request this build does not handle */
+  PGS_ERR_UNSUPPORTED = 6,   /* valid request this build does not handle */
+  PGS_ERR_BOUNDS = 7         /* an index failed a bounds check (bounds-checked build only; the access was skipped) */
 };
 
 #define PGS_MAX_VIEWS 32
@@ -189,6 +190,11 @@ typedef struct pgs_scene pgs_scene;
 
 const char* pgs_last_error(void);
 const char* pgs_status_string(pgs_status s);
+/* 1 in the bounds-checked build of the library (libpgs_checked.so, compiled
+ * with PGS_CHECKED: the blend, sort, emission and range kernels check their
+ * list, range, record and pixel indices against the scene's allocations and
+ * raise PGS_ERR_BOUNDS instead of accessing out of range), 0 otherwise. */
+int pgs_checked_build(void);
 void pgs_default_params(pgs_render_params* p);
 
 /* Validate the descriptor, allocate the workspace sized by its capacities.

@@ -14,9 +14,11 @@ from typing import Dict, List, Optional, Sequence
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libpgs.so")
+# PGS_LIB=checked selects the bounds-checked build (libpgs_checked.so); the default is the production library
+LIB_PATH = os.path.join(_HERE, "libpgs_checked.so" if os.environ.get("PGS_LIB") == "checked" else "libpgs.so")
 
-PGS_OK, PGS_ERR_INVALID_ARG, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE, PGS_ERR_CUDA, PGS_ERR_UNSUPPORTED = range(7)
+(PGS_OK, PGS_ERR_INVALID_ARG, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE, PGS_ERR_CUDA, PGS_ERR_UNSUPPORTED,
+ PGS_ERR_BOUNDS) = range(8)
 MODE_EXPLICIT, MODE_ANCHOR = 0, 1
 DECODE_FP32, DECODE_BF16, DECODE_BF16_1PASS = 0, 1, 2
 MAX_VIEWS = 32
@@ -36,7 +38,8 @@ def lib() -> C.CDLL:
     if _lib is None:
         if not os.path.exists(LIB_PATH):
             raise RuntimeError(f"CUDA library {LIB_PATH} is missing: build it with "
-                               "`python -m paper_2503_23044_b300.build` (no CPU fallback exists)")
+                               "`python -m paper_2503_23044_b300.build` (add --checked for the bounds-checked "
+                               "build; no CPU fallback exists)")
         _lib = C.CDLL(LIB_PATH)
         _declare(_lib)
     return _lib
@@ -125,7 +128,7 @@ ENTRY_POINTS = ("pgs_last_error", "pgs_status_string", "pgs_default_params", "pg
                 "pgs_get_stage_times", "pgs_scene_buffer", "pgs_sort_scratch_bytes", "pgs_sort_pairs",
                 "pgs_scan_scratch_bytes", "pgs_exclusive_scan_u32", "pgs_sort_pairs_noalloc", "pgs_autotune",
                 "pgs_scene_get_params", "pgs_filter_depth_prior", "pgs_ncc_loss_grad", "pgs_tsdf_integrate",
-                "pgs_scene_set_wait_limits")
+                "pgs_scene_set_wait_limits", "pgs_checked_build")
 STAGES = ("project", "depth_sort", "bin", "tile_sort", "blend_fwd", "loss", "blend_bwd", "project_bwd", "wgrad",
           "prior", "ncc", "tsdf")
 
@@ -153,6 +156,7 @@ def _declare(L: C.CDLL) -> None:
     L.pgs_read_status.argtypes = [vp, vp]
     L.pgs_get_stats.argtypes = [vp, P(Stats), vp]
     L.pgs_set_profiling.argtypes = [vp, i32]
+    L.pgs_checked_build.argtypes = []
     L.pgs_scene_set_wait_limits.argtypes = [vp, C.c_uint32, C.c_uint32]
     L.pgs_get_stage_times.argtypes = [vp, P(C.c_float), i32]
     L.pgs_scene_buffer.argtypes = [vp, i32, P(vp), P(i64)]

@@ -104,12 +104,14 @@ __device__ __forceinline__ void fwd_take(PixF& P, bool take, float power, float 
 }
 
 __device__ __forceinline__ void fwd_write(const PixF& P, const ViewDev& v, const ParamsDev& p, int px, int py,
-                                          uint32_t lo, const pgs_image_ptrs& out) {
+                                          uint32_t lo, const pgs_image_ptrs& out, long long total_pixels,
+                                          uint32_t* flags) {
   if (px >= v.W || py >= v.H) return;
   const float fx_rel = (float)px + 0.5f - v.cx, fy_rel = (float)py + 0.5f - v.cy;
   const long long HW = (long long)v.W * v.H;
   const long long q = v.pix_off + (long long)py * v.W + px;
   const long long q3 = 3 * v.pix_off + (long long)py * v.W + px;
+  if (!in_bounds(q < total_pixels, flags)) return;
   out.rgb[q3] = fmaf(P.T, p.bg, P.cr);
   out.rgb[q3 + HW] = fmaf(P.T, p.bg, P.cg);
   out.rgb[q3 + 2 * HW] = fmaf(P.T, p.bg, P.cb);
@@ -153,7 +155,8 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
   const int bx = block_origin(tx * TW), by = block_origin(ty * TH);
   const float ox = __fsub_rn((float)bx, v.cx), oy = __fsub_rn((float)by, v.cy);
   const float fxl = (float)(px - bx) + 0.5f, fyl0 = (float)(py0 - by) + 0.5f, fyl1 = fyl0 + 1.f;
-  const uint2 rg = ranges[tile];
+  uint2 rg = ranges[tile];
+  if (!in_bounds(rg.x <= rg.y && rg.y <= b.cap_pairs, b.flags)) rg = make_uint2(0u, 0u);
   const float a_min = b.p.alpha_min, a_max = b.p.alpha_max, t_min = b.p.t_min;
   PixF P0{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 < v.H)};
   PixF P1{1.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0u, 0u, rg.y, !(px < v.W && py0 + 1 < v.H)};
@@ -162,7 +165,10 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
 #pragma unroll
     for (int h = 0; h < NB / NT; ++h) {
       const uint32_t jj = start + threadIdx.x + h * NT;
-      if (jj < rg.y) stage_record(s, threadIdx.x + h * NT, rec, pair_g[jj], a_min, ox, oy);
+      if (jj < rg.y) {
+        const uint32_t g = pair_g[jj];
+        if (in_bounds(g < b.cap_g, b.flags)) stage_record(s, threadIdx.x + h * NT, rec, g, a_min, ox, oy);
+      }
     }
     __syncthreads();
     const int cnt = min((uint32_t)NB, rg.y - start);
@@ -184,8 +190,8 @@ __device__ __forceinline__ void blend_fwd_tile(const BatchDev& b, int tile, Blen
       fwd_take<STATS>(P1, t1, pw1, q.w, c, nn, j, a_max, t_min);
     }
   }
-  fwd_write(P0, v, b.p, px, py0, rg.x, out);
-  fwd_write(P1, v, b.p, px, py0 + 1, rg.x, out);
+  fwd_write(P0, v, b.p, px, py0, rg.x, out, b.total_pixels, b.flags);
+  fwd_write(P1, v, b.p, px, py0 + 1, rg.x, out, b.total_pixels, b.flags);
 }
 
 struct PixB {            // backward state of one pixel
@@ -196,7 +202,8 @@ struct PixB {            // backward state of one pixel
 };
 
 __device__ __forceinline__ void bwd_setup(PixB& P, const ViewDev& v, const ParamsDev& p, int px, int py, float fx_rel,
-                                          const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi) {
+                                          const pgs_image_ptrs& img, const pgs_image_grad_ptrs& gi,
+                                          long long total_pixels, uint32_t* flags) {
   P.fy = (float)py + 0.5f - v.cy;
   P.T = 1.f; P.last = 0;
   P.gC0 = P.gC1 = P.gC2 = P.gD = P.gN0 = P.gN1 = P.gN2 = 0.f;
@@ -205,6 +212,7 @@ __device__ __forceinline__ void bwd_setup(PixB& P, const ViewDev& v, const Param
   const long long HW = (long long)v.W * v.H;
   const long long q = v.pix_off + (long long)py * v.W + px;
   const long long q3 = 3 * v.pix_off + (long long)py * v.W + px;
+  if (!in_bounds(q < total_pixels, flags)) return;
   P.last = img.last[q];
   P.T = img.t_final[q];
   P.gC0 = gi.rgb[q3]; P.gC1 = gi.rgb[q3 + HW]; P.gC2 = gi.rgb[q3 + 2 * HW];
@@ -302,6 +310,69 @@ __device__ __forceinline__ void bwd_pair(const RecF& r, float2 mt, uint32_t j, b
   acc[5] += G;
 }
 
+// The two records A (list index jA = jB + 1, met first on the way down) and B
+// of a lane, packed half by half (A low, B high) for the f32x2 pair step.
+struct RecPair {
+  f2 mx, my, qx, qy, qz, qw, c0, c1, c2, c3, n0, n1, n2;
+  float ploA, ploB;
+};
+__device__ __forceinline__ RecPair pack_records(const RecF& a, float2 ma, const RecF& b, float2 mb) {
+  RecPair R;
+  R.mx = f2_make(ma.x, mb.x); R.my = f2_make(ma.y, mb.y);
+  R.qx = f2_make(a.q.x, b.q.x); R.qy = f2_make(a.q.y, b.q.y); R.qz = f2_make(a.q.z, b.q.z);
+  R.qw = f2_make(a.q.w, b.q.w);
+  R.c0 = f2_make(a.c.x, b.c.x); R.c1 = f2_make(a.c.y, b.c.y); R.c2 = f2_make(a.c.z, b.c.z);
+  R.c3 = f2_make(a.c.w, b.c.w);
+  R.n0 = f2_make(a.n.x, b.n.x); R.n1 = f2_make(a.n.y, b.n.y); R.n2 = f2_make(a.n.z, b.n.z);
+  R.ploA = a.n.w; R.ploB = b.n.w;
+  return R;
+}
+
+// bwd_pair for records A then B at one pixel, with every operation that does
+// not depend on the other record done on both halves at once (f32x2, each half
+// rounded as the scalar form, so alphas are the forward's bit for bit); the
+// transmittance and GS chain stays scalar (B sees A's update).
+__device__ __forceinline__ void bwd_pair2(const RecPair& R, uint32_t jA, uint32_t jB, bool actA, bool actB,
+                                          const float4 g0, const float4 g1, const float2 f, float& T, float& GS,
+                                          f2 (&acc)[kGradFields], float a_max) {
+  const f2 dx = f2_sub(f2_splat(f.x), R.mx), dy = f2_sub(f2_splat(f.y), R.my);
+  const f2 xx = f2_mul(dx, dx), xy = f2_mul(dx, dy), yy = f2_mul(dy, dy);
+  const f2 pw = f2_fma(R.qx, xx, f2_fma(R.qz, yy, f2_mul(R.qy, xy)));
+  const float pA = f2_lo(pw), pB = f2_hi(pw);
+  const uint32_t last = __float_as_uint(g1.w);
+  const bool tA = actA && jA < last && !(pA > 0.f) && pA >= R.ploA;
+  const bool tB = actB && jB < last && !(pB > 0.f) && pB >= R.ploB;
+  const f2 araw = f2_mul(R.qw, f2_make(ex2_approx(pA), ex2_approx(pB)));
+  const float arA = f2_lo(araw), arB = f2_hi(araw);
+  const float alA = fminf(a_max, arA), alB = fminf(a_max, arB);
+  const f2 om = f2_sub(f2_splat(1.f), f2_make(alA, alB));
+  const float iomA = rcp_approx(f2_lo(om)), iomB = rcp_approx(f2_hi(om));
+  f2 gf = f2_mul(f2_splat(g0.x), R.c0);
+  gf = f2_fma(f2_splat(g0.y), R.c1, gf); gf = f2_fma(f2_splat(g0.z), R.c2, gf); gf = f2_fma(f2_splat(g0.w), R.c3, gf);
+  gf = f2_fma(f2_splat(g1.x), R.n0, gf); gf = f2_fma(f2_splat(g1.y), R.n1, gf); gf = f2_fma(f2_splat(g1.z), R.n2, gf);
+  const float gfA = f2_lo(gf), gfB = f2_hi(gf);
+  const float T1 = tA ? T * iomA : T;
+  const float wA = tA ? alA * T1 : 0.f;
+  const float dA = fmaf(T1, gfA, -GS * iomA);
+  const float GS1 = fmaf(wA, gfA, GS);
+  const float T2 = tB ? T1 * iomB : T1;
+  const float wB = tB ? alB * T2 : 0.f;
+  const float dB = fmaf(T2, gfB, -GS1 * iomB);
+  GS = fmaf(wB, gfB, GS1);
+  T = T2;
+  const f2 w = f2_make(wA, wB);
+  acc[6] = f2_fma(w, f2_splat(g0.x), acc[6]); acc[7] = f2_fma(w, f2_splat(g0.y), acc[7]);
+  acc[8] = f2_fma(w, f2_splat(g0.z), acc[8]); acc[9] = f2_fma(w, f2_splat(g0.w), acc[9]);
+  acc[10] = f2_fma(w, f2_splat(g1.x), acc[10]); acc[11] = f2_fma(w, f2_splat(g1.y), acc[11]);
+  acc[12] = f2_fma(w, f2_splat(g1.z), acc[12]);
+  // alpha clamped at alpha_max carries no gradient to o, mean, conic
+  const float GA = (tA && !(arA > a_max)) ? dA * arA : 0.f;
+  const float GB = (tB && !(arB > a_max)) ? dB * arB : 0.f;
+  const f2 G = f2_make(GA, GB);
+  acc[0] = f2_fma(G, dx, acc[0]); acc[1] = f2_fma(G, dy, acc[1]); acc[2] = f2_fma(G, xx, acc[2]);
+  acc[3] = f2_fma(G, xy, acc[3]); acc[4] = f2_fma(G, yy, acc[4]); acc[5] = f2_add(acc[5], G);
+}
+
 // add one record's per-tile sums to its gradient row (nonzero float4 parts only)
 __device__ __forceinline__ void flush_record(const float acc[kGradFields], float4 q, uint32_t gid,
                                              float* __restrict__ grad) {
@@ -340,6 +411,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
   const int lane = threadIdx.x & 31;
   const uint2 rg = ranges[tile];
   if (rg.y <= rg.x) return;
+  if (!in_bounds(rg.y <= b.cap_pairs, b.flags)) return;
   const int vi = view_of_tile(b, tile);
   const ViewDev& v = b.v[vi];
   const int lt = tile - v.tile_base;
@@ -352,7 +424,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
     const int px = tx * TW + p % TW, py = ty * TH + p / TW;
     const float fx = (float)px + 0.5f - v.cx;
     PixB P;
-    bwd_setup(P, v, b.p, px, py, fx, img, gi);
+    bwd_setup(P, v, b.p, px, py, fx, img, gi, b.total_pixels, b.flags);
     tab.g0[p] = make_float4(P.gC0, P.gC1, P.gC2, P.gD);
     tab.g1[p] = make_float4(P.gN0, P.gN1, P.gN2, __uint_as_float(P.last));
     tab.f[p] = make_float2((float)(px - bx) + 0.5f, (float)(py - by) + 0.5f);
@@ -379,14 +451,16 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
       const int seg_lo = grp * seg, seg_hi = min(n_live, seg_lo + seg);
       const uint32_t jB = cbase + li + min(li, n2), jA = jB + 1;
       const bool hasA = li < n2;
-      const uint32_t gB = pair_g[jB], gA = hasA ? pair_g[jA] : 0u;
+      uint32_t gB = pair_g[jB], gA = hasA ? pair_g[jA] : 0u;
+      if (!in_bounds(gB < b.cap_g && gA < b.cap_g, b.flags)) gA = gB = 0u;
       const RecF rB = load_record(rec, gB, a_min);
       RecF rA{};
       if (hasA) rA = load_record(rec, gA, a_min);
       const float2 mtB = tile_mean(rB.m, ox, oy), mtA = tile_mean(rA.m, ox, oy);
-      float accA[kGradFields], accB[kGradFields];
+      const RecPair R = pack_records(rA, mtA, rB, mtB);
+      f2 acc[kGradFields];
 #pragma unroll
-      for (int f = 0; f < kGradFields; ++f) accA[f] = accB[f] = 0.f;
+      for (int f = 0; f < kGradFields; ++f) acc[f] = f2_splat(0.f);
       __syncwarp();
       float T = 0.f, GS = 0.f;
       const int nsteps = seg + 15;
@@ -406,14 +480,15 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
           T = t.x;
           GS = t.y;
         }
-        bwd_pair(rA, mtA, jA, act && hasA, g0, g1, f, T, GS, accA, a_max);
-        bwd_pair(rB, mtB, jB, act, g0, g1, f, T, GS, accB, a_max);
+        bwd_pair2(R, jA, jB, act && hasA, act, g0, g1, f, T, GS, acc, a_max);
         if (act && li == 0) tab.st[pix] = make_float2(T, GS);
       }
+      float accA[kGradFields], accB[kGradFields];
 #pragma unroll
       for (int f = 0; f < kGradFields; ++f) {
-        accA[f] += __shfl_xor_sync(FULL, accA[f], 16);
-        accB[f] += __shfl_xor_sync(FULL, accB[f], 16);
+        const f2 t = f2_add(acc[f], f2_shfl_xor(acc[f], 16));
+        accA[f] = f2_lo(t);
+        accB[f] = f2_hi(t);
       }
       if (grp == 0) {
         flush_record(accB, rB.q, gB, grad);
@@ -441,6 +516,7 @@ __device__ __forceinline__ void blend_bwd_tile(const BatchDev& b, int tile, BwdT
     RecF r{};
     if (has) {
       gid = pair_g[j];
+      if (!in_bounds(gid < b.cap_g, b.flags)) gid = 0u;
       r = load_record(rec, gid, a_min);
     }
     const float2 mt = tile_mean(r.m, ox, oy);
@@ -495,7 +571,9 @@ __global__ void __launch_bounds__(TW * TH / 2) k_blend_fwd(const __grid_constant
     __syncthreads();
     const uint32_t it = s_next;
     if (it >= (uint32_t)b.total_tiles) break;
-    blend_fwd_tile<TW, TH, NB, STATS>(b, (int)order[it], s, rec, pair_g, ranges, out);
+    const uint32_t tile = order[it];
+    if (!in_bounds(tile < (uint32_t)b.total_tiles, b.flags)) continue;
+    blend_fwd_tile<TW, TH, NB, STATS>(b, (int)tile, s, rec, pair_g, ranges, out);
   }
 }
 
@@ -515,7 +593,9 @@ __global__ void __launch_bounds__(32 * kBwdWarps) k_blend_bwd(const __grid_const
     if ((threadIdx.x & 31) == 0) it = atomicAdd(counter, 1u);
     it = __shfl_sync(0xffffffffu, it, 0);
     if (it >= (uint32_t)b.total_tiles) break;
-    blend_bwd_tile<TW>(b, (int)order[it], tab, rec, pair_g, ranges, img, gi, grad);
+    const uint32_t tile = order[it];
+    if (!in_bounds(tile < (uint32_t)b.total_tiles, b.flags)) continue;
+    blend_bwd_tile<TW>(b, (int)tile, tab, rec, pair_g, ranges, img, gi, grad);
   }
 }
 

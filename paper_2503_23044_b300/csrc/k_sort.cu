@@ -291,8 +291,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
       if (idx < n) {
         const uint32_t dg = (key[i] >> shift) & dmask;
         const uint32_t lp = s_excl[dg] + s_whist[warp][dg] + rank[i];
-        s_keys[lp] = key[i];
-        s_vals[lp] = val[i];
+        if (in_bounds(lp < (uint32_t)kSortTile, err)) {
+          s_keys[lp] = key[i];
+          s_vals[lp] = val[i];
+        }
       }
     }
     __syncthreads();
@@ -380,8 +382,9 @@ constexpr uint32_t kEmitBig = 96;
 // write pair (tid, g) at output position o of a warp whose window starts at wbase
 __device__ __forceinline__ void emit_one(long long o, long long wbase, uint32_t tid, uint32_t g, long long cap,
                                          uint32_t* s_t, uint32_t* s_g, uint32_t* __restrict__ tiles_out,
-                                         uint32_t* __restrict__ g_out) {
+                                         uint32_t* __restrict__ g_out, uint32_t* err) {
   const long long rel = o - wbase;
+  if (!in_bounds(rel >= 0, err)) return;
   if (rel < kEmitStage) {
     s_t[rel] = tid;
     s_g[rel] = g;
@@ -413,6 +416,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit_pairs(const __grid_con
     long long o = 0;
     if (ok) {
       g = sorted_g[k];
+      if (!in_bounds(g < (uint32_t)b.cap_g, err)) g = 0u;
       cnt = counts[g];
       o = offs[k];
     }
@@ -428,7 +432,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit_pairs(const __grid_con
         const int tb = v.tile_base, tx_n = v.tiles_x;
         for_each_tile_row(e, v, b.p.tile_w, b.p.tile_h, [&](int ty, int c0, int c1) {
           for (int tx = c0; tx <= c1; ++tx) {
-            if (o < o_end) emit_one(o, wbase, (uint32_t)(tb + ty * tx_n + tx), g, cap, s_t[w], s_g[w], tiles_out, g_out);
+            if (o < o_end) emit_one(o, wbase, (uint32_t)(tb + ty * tx_n + tx), g, cap, s_t[w], s_g[w], tiles_out, g_out, err);
             ++o;
           }
         });
@@ -464,7 +468,7 @@ __global__ void __launch_bounds__(32 * kEmitWarps) k_emit_pairs(const __grid_con
           }
           long long q = pos + (incl - rc);
           for (int tx = c0; tx <= c1; ++tx, ++q)
-            if (q < oe) emit_one(q, wbase, (uint32_t)(tb + ty * tx_n + tx), gb, cap, s_t[w], s_g[w], tiles_out, g_out);
+            if (q < oe) emit_one(q, wbase, (uint32_t)(tb + ty * tx_n + tx), gb, cap, s_t[w], s_g[w], tiles_out, g_out, err);
           pos += __shfl_sync(0xffffffffu, incl, 31);
         }
       }
@@ -492,10 +496,11 @@ __global__ void k_pairs_total(const unsigned long long* __restrict__ total, long
 }
 
 __global__ void k_tile_ranges(const uint32_t* __restrict__ tiles, const long long* __restrict__ d_p,
-                              uint2* __restrict__ ranges) {
+                              uint2* __restrict__ ranges, int n_tiles, uint32_t* err) {
   const long long P = *d_p;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < P; i += (long long)gridDim.x * blockDim.x) {
     const uint32_t t = tiles[i];
+    if (!in_bounds(t < (uint32_t)n_tiles, err)) continue;
     if (i == 0 || tiles[i - 1] != t) ranges[t].x = (uint32_t)i;
     if (i == P - 1 || tiles[i + 1] != t) ranges[t].y = (uint32_t)(i + 1);
   }

@@ -180,6 +180,8 @@ extern "C" {
 
 const char* pgs_last_error(void) { return g_last_error.c_str(); }
 
+int pgs_checked_build(void) { return kChecked ? 1 : 0; }
+
 const char* pgs_status_string(pgs_status s) {
   switch (s) {
     case PGS_OK: return "ok";
@@ -189,6 +191,7 @@ const char* pgs_status_string(pgs_status s) {
     case PGS_ERR_NONFINITE: return "non-finite value";
     case PGS_ERR_CUDA: return "CUDA error";
     case PGS_ERR_UNSUPPORTED: return "unsupported";
+    case PGS_ERR_BOUNDS: return "index out of bounds (checked build)";
     default: return "unknown status";
   }
 }
@@ -390,6 +393,9 @@ pgs_status build_batch(pgs_scene* s, const pgs_camera* cams, int n_views, BatchD
   if (tiles > s->max_tiles) return fail(PGS_ERR_INVALID_ARG, "batch has %lld tiles > %lld", tiles, s->max_tiles);
   b.total_tiles = (int)tiles;
   b.total_pixels = pix;
+  b.cap_pairs = s->cap_pairs;
+  b.cap_g = s->cap_g;
+  b.flags = s->d_flags;
   return PGS_OK;
 }
 
@@ -498,7 +504,7 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
                              s->ss, s->d_flags, s->spin_limit, s->hold_tile, ns, st, &nl));
   k_sort_timeout_guard<<<1, 32, 0, st>>>(s->d_flags, d_P, s->cap_pairs, nullptr);   // ran out: no pairs
   PGS_CUDA(cudaMemsetAsync(s->ranges, 0, (size_t)b.total_tiles * sizeof(uint2), st));
-  k_tile_ranges<<<ns * 8, 256, 0, st>>>(s->ptile_a, d_P, s->ranges);
+  k_tile_ranges<<<ns * 8, 256, 0, st>>>(s->ptile_a, d_P, s->ranges, b.total_tiles, s->d_flags);
   s->launches += nl + 2;
   // queue order for the persistent blend kernels: longest tile lists first
   k_set_i64<<<1, 1, 0, st>>>(s->d_cnt + 4, b.total_tiles);
@@ -815,7 +821,7 @@ pgs_status pgs_read_status(pgs_scene* s, cudaStream_t st) {
   f |= e2;
   PGS_CUDA(cudaMemset(s->d_flags, 0, sizeof(uint32_t)));
   PGS_CUDA(cudaMemset(s->ss.err, 0, sizeof(uint32_t)));
-  for (int c : {PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE})
+  for (int c : {PGS_ERR_BOUNDS, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE})
     if (f & (1u << c)) return fail(c, "device reported: %s", pgs_status_string(c));
   return PGS_OK;
 }

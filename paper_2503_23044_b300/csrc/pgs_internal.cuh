@@ -17,6 +17,7 @@ constexpr int kMaxIn = 36;
 constexpr uint32_t kFlagCapacity = 1u << PGS_ERR_CAPACITY;
 constexpr uint32_t kFlagTimeout = 1u << PGS_ERR_TIMEOUT;
 constexpr uint32_t kFlagNonfinite = 1u << PGS_ERR_NONFINITE;
+constexpr uint32_t kFlagBounds = 1u << PGS_ERR_BOUNDS;
 
 // log2(e): the blend evaluates alpha = o * 2^(log2e * power)
 constexpr float kLog2e = 1.4426950408889634f;
@@ -45,6 +46,8 @@ struct BatchDev {
   int n_views;
   int total_tiles;
   long long total_pixels;
+  long long cap_pairs, cap_g;   // allocated pair and Gaussian-view slots of the scene (bounds of the checked build)
+  uint32_t* flags;              // the scene's device error flags
 };
 
 // Gaussian-view record: 4 x float4 = 64 B
@@ -88,6 +91,20 @@ __device__ __forceinline__ float ex2_approx(float x) {
 }
 
 __device__ __forceinline__ void set_flag(uint32_t* flags, uint32_t bit) { atomicOr(flags, bit); }
+
+// Index checks of the bounds-checked build (compiled with -DPGS_CHECKED, library libpgs_checked.so): a
+// failing check raises PGS_ERR_BOUNDS in *flags and returns false, and the caller skips the access.  In the
+// production build every check is the constant true and costs nothing.
+#ifdef PGS_CHECKED
+constexpr bool kChecked = true;
+__device__ __forceinline__ bool in_bounds(bool ok, uint32_t* flags) {
+  if (!ok && flags) set_flag(flags, kFlagBounds);
+  return ok;
+}
+#else
+constexpr bool kChecked = false;
+__device__ __forceinline__ constexpr bool in_bounds(bool, uint32_t*) { return true; }
+#endif
 
 // ---- packed FP32 pairs (sm_100 family): add / sub / mul / fma .rn.f32x2 round each half exactly as the
 // scalar __fadd_rn / __fsub_rn / __fmul_rn / __fmaf_rn would, at one issue slot for both halves

@@ -94,7 +94,7 @@ __global__ void k_emit_pairs(const __grid_constant__ BatchDev b, const float4* r
                              int mode, long long n_explicit, const uint32_t* rows, uint32_t* tiles_out,
                              uint32_t* g_out, uint32_t* err);
 __global__ void k_pairs_total(const unsigned long long* total, long long cap, long long* d_p, uint32_t* err);
-__global__ void k_tile_ranges(const uint32_t* tiles, const long long* d_p, uint2* ranges);
+__global__ void k_tile_ranges(const uint32_t* tiles, const long long* d_p, uint2* ranges, int n_tiles, uint32_t* err);
 
 // k_blend.cu (persistent kernels: tiles taken from a queue in `order` via `ctr`, which must start at 0)
 bool launch_blend_fwd(const BatchDev& b, const float4* rec, const uint32_t* pg, const uint2* rg,
