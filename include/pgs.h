@@ -415,8 +415,9 @@ pgs_status pgs_scene_buffer(pgs_scene* s, int which, void** d_ptr, int64_t* capa
 /* Stand-alone stages of the reorder pi (Eq. 5), exposed for the integer
  * parity tests and for reuse.
  *
- * Stable LSD radix sort (one histogram pass, then one pass per 8-bit digit
- * with decoupled look-back) of n = *d_n (device int64, clamped to n_max)
+ * Stable LSD radix sort (one histogram pass, then one pass per 8-bit digit,
+ * or two 9-bit digits for ranges of 17-18 bits, one pass fewer;
+ * decoupled look-back) of n = *d_n (device int64, clamped to n_max)
  * key/value pairs on bits [bit_lo, bit_hi) of the keys.  The sorted result
  * ends in (d_keys, d_vals); d_keys_alt / d_vals_alt are ping-pong buffers of
  * the same size.  Scratch must hold pgs_sort_scratch_bytes(n_max) bytes.  A

@@ -126,7 +126,8 @@ constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
 static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch layout");
-constexpr int kRadix = 256;
+constexpr int kRadix = 256;          // digits of the 8-bit passes
+constexpr int kRadixMax = 512;       // digits of the 9-bit passes (ranges of 17-18 or 25-27 bits)
 constexpr uint32_t kStFlagAgg = 1u << 30, kStFlagInc = 2u << 30, kStMask = (1u << 30) - 1;
 
 __device__ __forceinline__ uint32_t ld_relaxed(const uint32_t* p) {
@@ -138,69 +139,79 @@ __device__ __forceinline__ void st_relaxed(uint32_t* p, uint32_t v) {
   asm volatile("st.relaxed.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// the last digit of a bit range that is not a multiple of 8 is narrower
-__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int bit_hi) {
-  const int w = bit_hi - shift < 8 ? bit_hi - shift : 8;
+// the last digit of a bit range that is not a multiple of the digit width is narrower
+__host__ __device__ __forceinline__ uint32_t digit_mask(int shift, int bit_hi, int rb = 8) {
+  const int w = bit_hi - shift < rb ? bit_hi - shift : rb;
   return (1u << w) - 1u;
 }
 
-SortScratch sort_scratch_layout(void* base, long long n_max) {
+SortScratch sort_scratch_layout(void* base, long long n_max, int radix_bits_max) {
   SortScratch s;
   char* p = static_cast<char*>(base);
-  s.hist = reinterpret_cast<uint32_t*>(p);                 // [4][256]
+  s.hist = reinterpret_cast<uint32_t*>(p);                 // [4][256] or [2][512]
   s.counters = s.hist + 4 * kRadix;                         // [4]
   s.err = s.counters + 4;                                   // [1] (+3 pad)
   s.max_tiles = (n_max + kSortTile - 1) / kSortTile + 1;
-  s.status = s.err + 4;                                     // [2][max_tiles][256]
-  s.bytes = sort_scratch_bytes_for(n_max);
+  s.status = s.err + 4;                                     // [2][max_tiles][256 or 512]
+  s.radix_bits_max = radix_bits_max;
+  s.bytes = sort_scratch_bytes_for(n_max, radix_bits_max);
   return s;
 }
 
+template <int RB>
 __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const long long* __restrict__ d_n,
                                                    long long n_max, int bit_lo, int bit_hi, int n_pass,
-                                                   uint32_t* __restrict__ hist, uint32_t* __restrict__ status0) {
-  __shared__ uint32_t s_h[4][kRadix];
-  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) (&s_h[0][0])[i] = 0;
+                                                   uint32_t* __restrict__ hist, uint32_t* __restrict__ status0,
+                                                   uint32_t* err) {
+  constexpr int R = 1 << RB;
+  __shared__ uint32_t s_h[4 * kRadix];                      // [n_pass][R], n_pass * R <= 1024
+  for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) s_h[i] = 0;
   __syncthreads();
   const long long n = max(0ll, min(*d_n, n_max));
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
     const uint32_t key = keys[k];
     for (int p = 0; p < n_pass; ++p) {
-      const int sh = bit_lo + 8 * p;
-      atomicAdd(&s_h[p][(key >> sh) & digit_mask(sh, bit_hi)], 1u);
+      const int sh = bit_lo + RB * p;
+      const uint32_t i = p * R + ((key >> sh) & digit_mask(sh, bit_hi, RB));
+      if (in_bounds(i < 4u * kRadix, err)) atomicAdd(&s_h[i], 1u);
     }
   }
   // clear the look-back status of the first pass for the live tiles
   const long long n_tiles = (n + kSortTile - 1) / kSortTile;
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_tiles * kRadix;
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n_tiles * R;
        k += (long long)gridDim.x * blockDim.x)
     status0[k] = 0;
   __syncthreads();
-  for (int i = threadIdx.x; i < n_pass * kRadix; i += blockDim.x) {
-    const uint32_t c = (&s_h[0][0])[i];
+  for (int i = threadIdx.x; i < n_pass * R; i += blockDim.x) {
+    const uint32_t c = s_h[i];
     if (c) atomicAdd(hist + i, c);
   }
 }
 
-__global__ void __launch_bounds__(kRadix) k_sort_hist_scan(uint32_t* __restrict__ hist, int n_pass) {
+// exclusive scan of each pass's digit counts: launched with R threads
+template <int RB>
+__global__ void __launch_bounds__(1 << RB) k_sort_hist_scan(uint32_t* __restrict__ hist, int n_pass) {
+  constexpr int R = 1 << RB;
   __shared__ unsigned long long s_w[33];
   for (int p = 0; p < n_pass; ++p) {
     unsigned long long tot;
-    const unsigned long long ex = block_exclusive_scan_u64(hist[p * kRadix + threadIdx.x], s_w, tot);
-    hist[p * kRadix + threadIdx.x] = (uint32_t)ex;
+    const unsigned long long ex = block_exclusive_scan_u64(hist[p * R + threadIdx.x], s_w, tot);
+    hist[p * R + threadIdx.x] = (uint32_t)ex;
   }
 }
 
+template <int RB>
 __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const long long* __restrict__ d_n, long long n_max, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
     uint32_t* __restrict__ status_next, uint32_t* __restrict__ err, uint32_t spin_limit, uint32_t hold_tile) {
+  constexpr int R = 1 << RB, DPT = R / kSortThreads;   // digits, digits per thread (1 or 2)
   __shared__ uint32_t s_keys[kSortTile];
   __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_whist[kSortWarps][kRadix];
-  __shared__ uint32_t s_excl[kRadix];
-  __shared__ uint32_t s_gbase[kRadix];
+  __shared__ uint32_t s_whist[kSortWarps][R];
+  __shared__ uint32_t s_excl[R];
+  __shared__ uint32_t s_gbase[R];
   __shared__ unsigned long long s_w[33];
   __shared__ uint32_t s_tile;
   const long long n = max(0ll, min(*d_n, n_max));
@@ -209,7 +220,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
   const uint32_t lt_mask = (1u << lane) - 1u;
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
-    for (int i = threadIdx.x; i < kSortWarps * kRadix; i += kSortThreads) (&s_whist[0][0])[i] = 0;
+    for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&s_whist[0][0])[i] = 0;
     __syncthreads();
     const long long tile = s_tile;
     if (tile >= n_tiles) break;
@@ -228,7 +239,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
       const long long idx = base + i * 32 + lane;
       const bool ok = idx < n;
       const uint32_t dg = (key[i] >> shift) & dmask;
-      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? dg : 0x100u + lane);
+      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? dg : 0x10000u + lane);   // no digit is >= 2^16
       const uint32_t before = s_whist[warp][dg];
       __syncwarp();
       rank[i] = before + __popc(peers & lt_mask);
@@ -236,54 +247,70 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
       __syncwarp();
     }
     __syncthreads();
-    const int d = threadIdx.x;
-    uint32_t run = 0;
+    // per digit d = DPT t + k of this thread: counts of the tile (warp order kept in s_whist)
+    uint32_t run[DPT];
 #pragma unroll
-    for (int w = 0; w < kSortWarps; ++w) {
-      const uint32_t c = s_whist[w][d];
-      s_whist[w][d] = run;
-      run += c;
-    }
-    uint32_t* st = status + tile * kRadix;
-    // (hold_tile: a failure-path test hook; that tile never publishes, so the next one's wait runs out)
-    if (tile != hold_tile) st_relaxed(st + d, (tile == 0 ? kStFlagInc : kStFlagAgg) | run);
-    unsigned long long tot;
-    const uint32_t excl = (uint32_t)block_exclusive_scan_u64(run, s_w, tot);
-    s_excl[d] = excl;
-    // decoupled look-back over earlier tiles, eight status words per round
-    // (independent loads), each wait bounded
-    uint32_t prefix = 0;
-    if (tile > 0) {
-      long long j = tile - 1;
-      uint32_t spins = 0;
-      bool stop = false;
-      while (!stop && j >= 0) {
-        constexpr int kLB = 8;
-        uint32_t w[kLB];
+    for (int k = 0; k < DPT; ++k) {
+      const int d = threadIdx.x * DPT + k;
+      uint32_t r = 0;
 #pragma unroll
-        for (int k = 0; k < kLB; ++k) w[k] = (j - k >= 0) ? ld_relaxed(status + (j - k) * kRadix + d) : kStFlagInc;
-#pragma unroll
-        for (int k = 0; k < kLB; ++k) {
-          if (stop) break;
-          uint32_t f = w[k] & ~kStMask;
-          while (f == 0u) {          // tile j - k has not published yet
-            if (++spins > spin_limit) { atomicOr(err, kFlagTimeout); break; }
-            if ((spins & 255u) == 0u && (ld_relaxed(err) & kFlagTimeout)) break;
-            __nanosleep(32);
-            w[k] = ld_relaxed(status + (j - k) * kRadix + d);
-            f = w[k] & ~kStMask;
-          }
-          if (f == 0u) { stop = true; break; }   // gave up (timeout flagged)
-          if (j - k < 0) { stop = true; break; }  // ran past tile 0
-          prefix += w[k] & kStMask;
-          if (f == kStFlagInc) stop = true;
-        }
-        j -= kLB;
+      for (int w = 0; w < kSortWarps; ++w) {
+        const uint32_t c = s_whist[w][d];
+        s_whist[w][d] = r;
+        r += c;
       }
-      if (tile != hold_tile) st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
+      run[k] = r;
     }
-    s_gbase[d] = digit_off[d] + prefix - excl;
-    if (status_next) status_next[tile * kRadix + d] = 0u;
+    uint32_t* st = status + tile * R;
+    // (hold_tile: a failure-path test hook; that tile never publishes, so the next one's wait runs out)
+#pragma unroll
+    for (int k = 0; k < DPT; ++k)
+      if (tile != hold_tile) st_relaxed(st + threadIdx.x * DPT + k, (tile == 0 ? kStFlagInc : kStFlagAgg) | run[k]);
+    uint32_t lsum = 0;
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) lsum += run[k];
+    unsigned long long tot;
+    uint32_t excl = (uint32_t)block_exclusive_scan_u64(lsum, s_w, tot);
+#pragma unroll
+    for (int k = 0; k < DPT; ++k) {
+      const int d = threadIdx.x * DPT + k;
+      s_excl[d] = excl;
+      // decoupled look-back over earlier tiles, eight status words per round
+      // (independent loads), each wait bounded
+      uint32_t prefix = 0;
+      if (tile > 0) {
+        long long j = tile - 1;
+        uint32_t spins = 0;
+        bool stop = false;
+        while (!stop && j >= 0) {
+          constexpr int kLB = 8;
+          uint32_t w[kLB];
+#pragma unroll
+          for (int q = 0; q < kLB; ++q) w[q] = (j - q >= 0) ? ld_relaxed(status + (j - q) * R + d) : kStFlagInc;
+#pragma unroll
+          for (int q = 0; q < kLB; ++q) {
+            if (stop) break;
+            uint32_t f = w[q] & ~kStMask;
+            while (f == 0u) {          // tile j - q has not published yet
+              if (++spins > spin_limit) { atomicOr(err, kFlagTimeout); break; }
+              if ((spins & 255u) == 0u && (ld_relaxed(err) & kFlagTimeout)) break;
+              __nanosleep(32);
+              w[q] = ld_relaxed(status + (j - q) * R + d);
+              f = w[q] & ~kStMask;
+            }
+            if (f == 0u) { stop = true; break; }   // gave up (timeout flagged)
+            if (j - q < 0) { stop = true; break; }  // ran past tile 0
+            prefix += w[q] & kStMask;
+            if (f == kStFlagInc) stop = true;
+          }
+          j -= kLB;
+        }
+        if (tile != hold_tile) st_relaxed(st + d, kStFlagInc | ((prefix + run[k]) & kStMask));
+      }
+      s_gbase[d] = digit_off[d] + prefix - excl;
+      if (status_next) status_next[tile * R + d] = 0u;
+      excl += run[k];
+    }
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
@@ -320,6 +347,12 @@ __global__ void k_copy_pairs(const uint32_t* __restrict__ ks, const uint32_t* __
   }
 }
 
+// digit width of a sort: 9 bits where that saves a pass and the scratch allows it.  The histogram area
+// holds 4 x 256 = 2 x 512 digit counts, so 9-bit digits are taken for two passes only (17-18 bits).
+static int sort_digit_bits(int bit_lo, int bit_hi, int radix_bits_max) {
+  const int bits = bit_hi - bit_lo;
+  return (radix_bits_max >= 9 && bits > 16 && bits <= 18) ? 9 : 8;
+}
 int sort_passes(int bit_lo, int bit_hi) { return (bit_hi - bit_lo + 7) / 8; }
 
 // After a sort whose look-back wait ran out (kFlagTimeout set) the output may
@@ -337,35 +370,49 @@ __global__ void k_sort_timeout_guard(const uint32_t* __restrict__ flags, long lo
     vals[i] = (uint32_t)i;
 }
 
-cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
-                              const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
-                              uint32_t* err, uint32_t spin_limit, uint32_t hold_tile, int num_sms, cudaStream_t st,
-                              int* n_launch) {
-  const int np = sort_passes(bit_lo, bit_hi);
+template <int RB>
+static cudaError_t launch_sort_rb(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                                  const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
+                                  uint32_t* err, uint32_t spin_limit, uint32_t hold_tile, int num_sms, cudaStream_t st,
+                                  int* n_launch) {
+  constexpr int R = 1 << RB;
+  const int np = (bit_hi - bit_lo + RB - 1) / RB;
   if (n_launch) *n_launch = 0;
   if (np <= 0) return cudaSuccess;
+  if (np * R > 4 * kRadix) return cudaErrorInvalidValue;   // more digit counts than the histogram area holds
   if (n_launch) *n_launch = 2 + np + (np & 1);
   cudaError_t e = cudaMemsetAsync(s.hist, 0, (size_t)(4 * kRadix + 4) * 4, st);
   if (e != cudaSuccess) return e;
-  uint32_t* status[2] = {s.status, s.status + (size_t)s.max_tiles * kRadix};
-  k_sort_hist<<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0]);
-  k_sort_hist_scan<<<1, kRadix, 0, st>>>(s.hist, np);
+  uint32_t* status[2] = {s.status, s.status + (size_t)s.max_tiles * R};
+  k_sort_hist<RB><<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0], err);
+  k_sort_hist_scan<RB><<<1, R, 0, st>>>(s.hist, np);
   // persistent passes: one resident wave (tiles are taken from a counter)
-  const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_sort_pass), kSortThreads, 0, 100);
+  const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_sort_pass<RB>), kSortThreads, 0, 100);
   const int pass_grid = (int)std::max(1ll, std::min((long long)per_sm * num_sms, (n_max + kSortTile - 1) / kSortTile));
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int p = 0; p < np; ++p) {
-    k_sort_pass<<<pass_grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + 8 * p,
-                                                     digit_mask(bit_lo + 8 * p, bit_hi), s.hist + p * kRadix,
-                                                     s.counters + p, status[p & 1],
-                                                     p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit,
-                                                     hold_tile);
+    k_sort_pass<RB><<<pass_grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + RB * p,
+                                                        digit_mask(bit_lo + RB * p, bit_hi, RB), s.hist + p * R,
+                                                        s.counters + p, status[p & 1],
+                                                        p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit,
+                                                        hold_tile);
     uint32_t* t;
     t = ki; ki = ko; ko = t;
     t = vi; vi = vo; vo = t;
   }
   if (ki != keys) k_copy_pairs<<<num_sms * 4, 256, 0, st>>>(ki, vi, keys, vals, d_n, n_max);
   return cudaGetLastError();
+}
+
+cudaError_t launch_sort_pairs(uint32_t* keys, uint32_t* vals, uint32_t* keys_alt, uint32_t* vals_alt,
+                              const long long* d_n, long long n_max, int bit_lo, int bit_hi, const SortScratch& s,
+                              uint32_t* err, uint32_t spin_limit, uint32_t hold_tile, int num_sms, cudaStream_t st,
+                              int* n_launch) {
+  if (sort_digit_bits(bit_lo, bit_hi, s.radix_bits_max) == 9)
+    return launch_sort_rb<9>(keys, vals, keys_alt, vals_alt, d_n, n_max, bit_lo, bit_hi, s, err, spin_limit,
+                             hold_tile, num_sms, st, n_launch);
+  return launch_sort_rb<8>(keys, vals, keys_alt, vals_alt, d_n, n_max, bit_lo, bit_hi, s, err, spin_limit, hold_tile,
+                           num_sms, st, n_launch);
 }
 
 // ------------------------------------------------------------------ pair emission and tile ranges

@@ -269,7 +269,7 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
   s->max_tiles = d.max_pixels / 64 + (long long)d.max_views * 1024;
   s->n_cull = d.mode == PGS_MODE_ANCHOR ? N * d.max_views : 0;
   const long long sort_n = std::max(std::max(s->cap_g, s->cap_pairs), s->max_tiles);
-  s->ss = sort_scratch_layout(nullptr, sort_n);
+  s->ss = sort_scratch_layout(nullptr, sort_n, 9);
   cudaError_t e = cudaSuccess;
 #define ALLOC(ptr, n) if (e == cudaSuccess) e = dmalloc(&(ptr), (size_t)(n))
   ALLOC(s->rec, s->cap_g * kRecF4);
@@ -317,7 +317,7 @@ pgs_status pgs_scene_create(const pgs_scene_desc* desc, pgs_scene** out) {
     pgs_scene_destroy(s);
     return fail(PGS_ERR_CUDA, "workspace allocation: %s", cudaGetErrorString(e));
   }
-  s->ss = sort_scratch_layout(s->sort_mem, sort_n);
+  s->ss = sort_scratch_layout(s->sort_mem, sort_n, 9);
   e = cudaMemset(s->d_flags, 0, 4 * sizeof(uint32_t));
   if (e == cudaSuccess) e = cudaMemset(s->d_cnt, 0, 8 * sizeof(long long));
   if (e == cudaSuccess) e = cudaMemset(s->ss.err, 0, sizeof(uint32_t));
@@ -858,7 +858,7 @@ pgs_status pgs_scene_buffer(pgs_scene* s, int which, void** d_ptr, int64_t* cap)
   return PGS_OK;
 }
 
-size_t pgs_sort_scratch_bytes(int64_t n_max) { return sort_scratch_layout(nullptr, n_max).bytes; }
+size_t pgs_sort_scratch_bytes(int64_t n_max) { return sort_scratch_layout(nullptr, n_max, 9).bytes; }
 
 pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_alt, uint32_t* d_vals_alt,
                           const int64_t* d_n, int64_t n_max, int bit_lo, int bit_hi, void* d_scratch,
@@ -868,7 +868,7 @@ pgs_status pgs_sort_pairs(uint32_t* d_keys, uint32_t* d_vals, uint32_t* d_keys_a
   if (n_max < 0 || n_max >= (1ll << 30)) return fail(PGS_ERR_INVALID_ARG, "n_max must be in [0, 2^30)");
   if (bit_lo < 0 || bit_hi > 32 || bit_lo >= bit_hi)
     return fail(PGS_ERR_INVALID_ARG, "bit range [%d, %d)", bit_lo, bit_hi);
-  SortScratch ss = sort_scratch_layout(d_scratch, n_max);
+  SortScratch ss = sort_scratch_layout(d_scratch, n_max, 9);
   if (scratch_bytes < ss.bytes) return fail(PGS_ERR_INVALID_ARG, "scratch %zu < %zu bytes", scratch_bytes, ss.bytes);
   const int ns = device_sm_count();
   PGS_CUDA(launch_sort_pairs(d_keys, d_vals, d_keys_alt, d_vals_alt, reinterpret_cast<const long long*>(d_n), n_max,

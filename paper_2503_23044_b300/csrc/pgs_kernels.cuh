@@ -37,6 +37,7 @@ struct SortScratch {
   uint32_t* err;
   uint32_t* status;
   long long max_tiles;
+  int radix_bits_max;   // 8, or 9 when the status arrays have room for 512 digits per tile
   size_t bytes;
 };
 
@@ -74,12 +75,14 @@ cudaError_t launch_decode_project_tc(bool split, const BatchDev& b, const pgs_an
 void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
                            const long long* d_n, unsigned long long* sums, cudaStream_t st);
 // keys per onesweep tile; the scratch layout below holds two look-back status
-// arrays of (n_max / kSortTileKeys + 1) x 256 words after the histograms
+// arrays of (n_max / kSortTileKeys + 1) x (1 << radix_bits_max) words after the histograms
+// (radix_bits_max 9 lets ranges of 17-18 bits sort in two 9-bit passes instead of three 8-bit ones)
 constexpr int kSortTileKeys = 2048;
-constexpr size_t sort_scratch_bytes_for(long long n_max) {
-  return (size_t)(4 * 256 + 8) * 4 + (size_t)2 * ((n_max + kSortTileKeys - 1) / kSortTileKeys + 1) * 256 * 4;
+constexpr size_t sort_scratch_bytes_for(long long n_max, int radix_bits_max = 8) {
+  return (size_t)(4 * 256 + 8) * 4 +
+         (size_t)2 * ((n_max + kSortTileKeys - 1) / kSortTileKeys + 1) * (size_t)(1 << radix_bits_max) * 4;
 }
-SortScratch sort_scratch_layout(void* base, long long n_max);
+SortScratch sort_scratch_layout(void* base, long long n_max, int radix_bits_max = 8);
 int sort_passes(int bit_lo, int bit_hi);
 // hold_tile: failure-path test hook (kNoHoldTile in production): that onesweep tile never publishes its
 // look-back status, so the next tile's bounded wait runs out and raises kFlagTimeout.

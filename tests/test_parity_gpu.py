@@ -22,8 +22,9 @@ MAX_FLAGGED = 0.01
 
 # ------------------------------------------------------------------ integer stages
 @pytest.mark.parametrize("n", [0, 1, 31, 4095, 4096, 4097, 100_003, 1 << 20])
-@pytest.mark.parametrize("bits", [(0, 32), (0, 16), (0, 17), (5, 29)])
+@pytest.mark.parametrize("bits", [(0, 32), (0, 16), (0, 17), (0, 18), (3, 29), (5, 29)])
 def test_sort_pairs_bitexact(n, bits):
+    """8-bit digits for 32, 16, 24 and 26 bits; two 9-bit digits (one pass fewer) for 17 and 18 bits."""
     rng = np.random.default_rng(n + bits[1])
     keys = rng.integers(0, 1 << 32, n, dtype=np.uint64).astype(np.uint32)
     if n > 100:                                       # many equal digits exercise stability
