@@ -275,7 +275,7 @@ pgs_status pgs_set_profiling(pgs_scene* s, int enable);
  * index order, no pairs, tiles in index order), so every later call of the
  * step returns and the context stays usable, but the images and gradients of
  * that step are meaningless.  withhold_tile is a failure-path test hook: the
- * onesweep tile (2048 keys) with this index never publishes its look-back
+ * onesweep tile (4096 keys) with this index never publishes its look-back
  * status in any pass, so the next tile's wait runs out; PGS_NO_WITHHELD_TILE
  * (the default) publishes every tile.  Applies to later calls on this scene. */
 #define PGS_NO_WITHHELD_TILE 0xffffffffu
@@ -323,7 +323,11 @@ pgs_status pgs_autotune(pgs_scene* s, const pgs_camera* cams, int n_views, const
  * depth prior and mask), d_scale_shift float[n_views][2] ((1, 0) for a view
  * with fewer than two usable points), d_err_out [pixels] optional (E, or -1
  * where unchecked).  k_neighbors in 1..4 (clamped to n_views - 1), tau_d > 0
- * in pixels.  Uses the scene's render parameters (near plane) and workspace. */
+ * in pixels.  Uses the scene's render parameters (near plane) and a
+ * workspace area of its own: it reads nothing that pgs_render_batch writes,
+ * so it may run on another stream concurrently with the render (the loss
+ * that reads its outputs must then wait for it); any other two calls on one
+ * scene must be ordered. */
 typedef struct pgs_prior_params {
   float tau_d;
   int32_t k_neighbors;

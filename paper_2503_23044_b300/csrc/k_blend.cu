@@ -657,13 +657,14 @@ bool launch_blend_bwd(const BatchDev& b, const float4* rec, const uint32_t* pg, 
   return true;
 }
 
-// Queue order of the tiles: descending list length (ties keep tile order).
+// Queue order of the tiles: descending list length (ties keep tile order), as a
+// 16-bit key (two sort passes); lists of 65,535 pairs or more share the first place.
 __global__ void k_tile_order_keys(const uint2* __restrict__ ranges, int n_tiles, uint32_t* __restrict__ keys,
                                   uint32_t* __restrict__ vals) {
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < n_tiles; t += gridDim.x * blockDim.x) {
     const uint2 r = ranges[t];
     const uint32_t len = r.y > r.x ? r.y - r.x : 0u;
-    keys[t] = 0xffffffu - min(len, 0xffffffu);
+    keys[t] = 0xffffu - min(len, 0xffffu);
     vals[t] = (uint32_t)t;
   }
 }

@@ -6,7 +6,7 @@
 // tiles are emitted in depth order and the pairs are stably sorted by tile id
 // only.  Both stages use the same onesweep pass (global digit histogram once,
 // then one pass per 8-bit digit with a decoupled look-back across tiles of
-// 2048 keys).  Every spin in the look-back is bounded: past the limit the pass
+// 4096 keys).  Every spin in the look-back is bounded: past the limit the pass
 // raises PGS_ERR_TIMEOUT and carries on, so no launch can hang.
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
@@ -121,10 +121,10 @@ void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* 
 }
 
 // ------------------------------------------------------------------ onesweep radix sort
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortWarps = kSortThreads / 32;
 constexpr int kSortItems = 8;
-constexpr int kSortTile = kSortThreads * kSortItems;   // 2048 keys per tile
+constexpr int kSortTile = kSortThreads * kSortItems;   // 4096 keys per tile
 static_assert(kSortTile == kSortTileKeys, "tile size shared with the scratch layout");
 constexpr int kRadix = 256;          // digits of the 8-bit passes
 constexpr int kRadixMax = 512;       // digits of the 9-bit passes (ranges of 17-18 or 25-27 bits)
@@ -200,16 +200,25 @@ __global__ void __launch_bounds__(1 << RB) k_sort_hist_scan(uint32_t* __restrict
   }
 }
 
+// One onesweep pass: 512 threads (two CTAs per SM) rank a tile of 4096 keys.
+// Larger tiles halve the tiles in flight against 2048-key tiles, and with them the
+// length of the look-back walks (about forty predecessors per digit and tile at
+// 2048 keys on the 14M-pair tile sort).  The eight digit matches of a warp are
+// issued back to back, then the per-warp running counts (16-bit: at most 4096)
+// are taken in item order, which keeps the ranking stable.  Keys and values
+// are reordered through dynamic shared memory (32 KB).
 template <int RB>
-__global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
+__global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(
     const uint32_t* __restrict__ kin, const uint32_t* __restrict__ vin, uint32_t* __restrict__ kout,
     uint32_t* __restrict__ vout, const long long* __restrict__ d_n, long long n_max, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_off, uint32_t* __restrict__ counter, uint32_t* __restrict__ status,
     uint32_t* __restrict__ status_next, uint32_t* __restrict__ err, uint32_t spin_limit, uint32_t hold_tile) {
-  constexpr int R = 1 << RB, DPT = R / kSortThreads;   // digits, digits per thread (1 or 2)
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
-  __shared__ uint32_t s_whist[kSortWarps][R];
+  constexpr int R = 1 << RB;   // digits: one per thread t < R
+  static_assert(R <= kSortThreads, "one digit per thread");
+  extern __shared__ uint32_t s_dyn[];
+  uint32_t* s_keys = s_dyn;
+  uint32_t* s_vals = s_dyn + kSortTile;
+  __shared__ uint16_t s_whist[kSortWarps][R];
   __shared__ uint32_t s_excl[R];
   __shared__ uint32_t s_gbase[R];
   __shared__ unsigned long long s_w[33];
@@ -233,47 +242,44 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
       key[i] = ok ? kin[idx] : 0xffffffffu;
       val[i] = ok ? vin[idx] : 0u;
     }
-    // warp-level stable ranking, item order (i, lane)
+    // warp-level stable ranking, item order (i, lane); no digit is >= 2^16, so padding lanes match no one
+#pragma unroll
+    for (int i = 0; i < kSortItems; ++i) {
+      const long long idx = base + i * 32 + lane;
+      const uint32_t dg = (key[i] >> shift) & dmask;
+      rank[i] = __match_any_sync(0xffffffffu, idx < n ? dg : 0x10000u + lane);
+    }
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {
       const long long idx = base + i * 32 + lane;
       const bool ok = idx < n;
       const uint32_t dg = (key[i] >> shift) & dmask;
-      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? dg : 0x10000u + lane);   // no digit is >= 2^16
+      const uint32_t peers = rank[i];
       const uint32_t before = s_whist[warp][dg];
       __syncwarp();
       rank[i] = before + __popc(peers & lt_mask);
-      if (ok && (peers & lt_mask) == 0) s_whist[warp][dg] = before + __popc(peers);
+      if (ok && (peers & lt_mask) == 0) s_whist[warp][dg] = (uint16_t)(before + __popc(peers));
       __syncwarp();
     }
     __syncthreads();
-    // per digit d = DPT t + k of this thread: counts of the tile (warp order kept in s_whist)
-    uint32_t run[DPT];
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) {
-      const int d = threadIdx.x * DPT + k;
-      uint32_t r = 0;
+    // digit d = t of the first R threads: counts of the tile (warp order kept in s_whist)
+    const int d = threadIdx.x;
+    const bool dthr = d < R;
+    uint32_t run = 0;
+    if (dthr) {
 #pragma unroll
       for (int w = 0; w < kSortWarps; ++w) {
         const uint32_t c = s_whist[w][d];
-        s_whist[w][d] = r;
-        r += c;
+        s_whist[w][d] = (uint16_t)run;
+        run += c;
       }
-      run[k] = r;
     }
     uint32_t* st = status + tile * R;
     // (hold_tile: a failure-path test hook; that tile never publishes, so the next one's wait runs out)
-#pragma unroll
-    for (int k = 0; k < DPT; ++k)
-      if (tile != hold_tile) st_relaxed(st + threadIdx.x * DPT + k, (tile == 0 ? kStFlagInc : kStFlagAgg) | run[k]);
-    uint32_t lsum = 0;
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) lsum += run[k];
+    if (dthr && tile != hold_tile) st_relaxed(st + d, (tile == 0 ? kStFlagInc : kStFlagAgg) | run);
     unsigned long long tot;
-    uint32_t excl = (uint32_t)block_exclusive_scan_u64(lsum, s_w, tot);
-#pragma unroll
-    for (int k = 0; k < DPT; ++k) {
-      const int d = threadIdx.x * DPT + k;
+    const uint32_t excl = (uint32_t)block_exclusive_scan_u64(run, s_w, tot);
+    if (dthr) {
       s_excl[d] = excl;
       // decoupled look-back over earlier tiles, eight status words per round
       // (independent loads), each wait bounded
@@ -305,11 +311,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) k_sort_pass(
           }
           j -= kLB;
         }
-        if (tile != hold_tile) st_relaxed(st + d, kStFlagInc | ((prefix + run[k]) & kStMask));
+        if (tile != hold_tile) st_relaxed(st + d, kStFlagInc | ((prefix + run) & kStMask));
       }
       s_gbase[d] = digit_off[d] + prefix - excl;
       if (status_next) status_next[tile * R + d] = 0u;
-      excl += run[k];
     }
     __syncthreads();
 #pragma unroll
@@ -387,11 +392,12 @@ static cudaError_t launch_sort_rb(uint32_t* keys, uint32_t* vals, uint32_t* keys
   k_sort_hist<RB><<<num_sms * 4, 256, 0, st>>>(keys, d_n, n_max, bit_lo, bit_hi, np, s.hist, status[0], err);
   k_sort_hist_scan<RB><<<1, R, 0, st>>>(s.hist, np);
   // persistent passes: one resident wave (tiles are taken from a counter)
-  const int per_sm = resident_ctas_per_sm(reinterpret_cast<const void*>(k_sort_pass<RB>), kSortThreads, 0, 100);
+  const size_t dsm = 2 * kSortTile * sizeof(uint32_t);
+  const int per_sm = prepare_smem_kernel(reinterpret_cast<const void*>(k_sort_pass<RB>), kSortThreads, dsm);
   const int pass_grid = (int)std::max(1ll, std::min((long long)per_sm * num_sms, (n_max + kSortTile - 1) / kSortTile));
   uint32_t *ki = keys, *vi = vals, *ko = keys_alt, *vo = vals_alt;
   for (int p = 0; p < np; ++p) {
-    k_sort_pass<RB><<<pass_grid, kSortThreads, 0, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + RB * p,
+    k_sort_pass<RB><<<pass_grid, kSortThreads, dsm, st>>>(ki, vi, ko, vo, d_n, n_max, bit_lo + RB * p,
                                                         digit_mask(bit_lo + RB * p, bit_hi, RB), s.hist + p * R,
                                                         s.counters + p, status[p & 1],
                                                         p + 1 < np ? status[(p + 1) & 1] : nullptr, err, spin_limit,

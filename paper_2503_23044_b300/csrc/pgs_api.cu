@@ -506,10 +506,11 @@ pgs_status pgs_render_batch(pgs_scene* s, const pgs_camera* cams, int n_views, c
   PGS_CUDA(cudaMemsetAsync(s->ranges, 0, (size_t)b.total_tiles * sizeof(uint2), st));
   k_tile_ranges<<<ns * 8, 256, 0, st>>>(s->ptile_a, d_P, s->ranges, b.total_tiles, s->d_flags);
   s->launches += nl + 2;
-  // queue order for the persistent blend kernels: longest tile lists first
+  // queue order for the persistent blend kernels: longest tile lists first (16-bit keys, two passes)
+  constexpr int kTileOrderBits = 16;
   k_set_i64<<<1, 1, 0, st>>>(s->d_cnt + 4, b.total_tiles);
   k_tile_order_keys<<<ns * 2, 256, 0, st>>>(s->ranges, b.total_tiles, s->order_k, s->order_v);
-  PGS_CUDA(launch_sort_pairs(s->order_k, s->order_v, s->order_kb, s->order_vb, s->d_cnt + 4, s->max_tiles, 0, 24,
+  PGS_CUDA(launch_sort_pairs(s->order_k, s->order_v, s->order_kb, s->order_vb, s->d_cnt + 4, s->max_tiles, 0, kTileOrderBits,
                              s->ss, s->d_flags, s->spin_limit, s->hold_tile, ns, st, &nl));
   k_sort_timeout_guard<<<ns, 256, 0, st>>>(s->d_flags, s->d_cnt + 4, s->max_tiles, s->order_v);  // ran out: tile order
   s->launches += 3 + nl;

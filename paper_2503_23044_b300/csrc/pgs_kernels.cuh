@@ -77,7 +77,7 @@ void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* 
 // keys per onesweep tile; the scratch layout below holds two look-back status
 // arrays of (n_max / kSortTileKeys + 1) x (1 << radix_bits_max) words after the histograms
 // (radix_bits_max 9 lets ranges of 17-18 bits sort in two 9-bit passes instead of three 8-bit ones)
-constexpr int kSortTileKeys = 2048;
+constexpr int kSortTileKeys = 4096;
 constexpr size_t sort_scratch_bytes_for(long long n_max, int radix_bits_max = 8) {
   return (size_t)(4 * 256 + 8) * 4 +
          (size_t)2 * ((n_max + kSortTileKeys - 1) / kSortTileKeys + 1) * (size_t)(1 << radix_bits_max) * 4;

@@ -52,7 +52,7 @@ def test_sort_wait_that_runs_out_is_reported_and_the_scene_recovers(mode):
     _step(scene, cams, ref, tg, B.ImageGrads.empty(ref.offsets[-1]), pg)
     scene.read_status()
     st = scene.stats()
-    assert st.gaussian_views > 2 * 2048 and st.pairs > 2 * 2048   # both sorts span several onesweep tiles
+    assert st.gaussian_views > 2 * 4096 and st.pairs > 2 * 4096   # both sorts span several onesweep tiles
     # tile 0 never publishes; tile 1 gives up after 64 polls
     scene.set_wait_limits(spin_limit=64, withhold_tile=0)
     img = B.Images.empty(cams)
