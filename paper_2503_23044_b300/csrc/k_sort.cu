@@ -200,12 +200,25 @@ __global__ void __launch_bounds__(1 << RB) k_sort_hist_scan(uint32_t* __restrict
   }
 }
 
+// the lanes of `valid` whose RB-bit digit equals this lane's: one ballot per digit bit
+// (warp-collective: every lane of the warp must call it, outside any per-lane condition)
+template <int RB>
+__device__ __forceinline__ uint32_t digit_peers(uint32_t dg, uint32_t valid) {
+  uint32_t peers = valid;
+#pragma unroll
+  for (int bit = 0; bit < RB; ++bit) {
+    const uint32_t bv = __ballot_sync(0xffffffffu, (dg >> bit) & 1u);
+    peers &= ~(bv ^ (0u - ((dg >> bit) & 1u)));
+  }
+  return peers;
+}
+
 // One onesweep pass: 512 threads (two CTAs per SM) rank a tile of 4096 keys.
 // Larger tiles halve the tiles in flight against 2048-key tiles, and with them the
 // length of the look-back walks (about forty predecessors per digit and tile at
-// 2048 keys on the 14M-pair tile sort).  The eight digit matches of a warp are
-// issued back to back, then the per-warp running counts (16-bit: at most 4096)
-// are taken in item order, which keeps the ranking stable.  Keys and values
+// 2048 keys on the 14M-pair tile sort).  The eight peer masks of a warp are
+// formed first, then the per-warp running counts (16-bit: at most 4096) are
+// taken in item order, which keeps the ranking stable.  Keys and values
 // are reordered through dynamic shared memory (32 KB).
 template <int RB>
 __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(
@@ -227,6 +240,7 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(
   const long long n_tiles = (n + kSortTile - 1) / kSortTile;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const uint32_t lt_mask = (1u << lane) - 1u;
+  const bool top_pass = status_next == nullptr;        // the last pass has no next status to clear
   for (;;) {
     if (threadIdx.x == 0) s_tile = atomicAdd(counter, 1u);
     for (int i = threadIdx.x; i < kSortWarps * R; i += kSortThreads) (&s_whist[0][0])[i] = 0;
@@ -242,12 +256,28 @@ __global__ void __launch_bounds__(kSortThreads, 2) k_sort_pass(
       key[i] = ok ? kin[idx] : 0xffffffffu;
       val[i] = ok ? vin[idx] : 0u;
     }
-    // warp-level stable ranking, item order (i, lane); no digit is >= 2^16, so padding lanes match no one
+    // warp-level stable ranking, item order (i, lane).  The lanes holding the same digit
+    // (padding lanes match no one) come from one ballot per digit bit: `match.any`
+    // serialises over the distinct digits of a warp, which the low digits of the tile
+    // sort have many of.  In the top pass (the most significant digit, often one per
+    // warp) a warp whose 32 digits agree skips the ballots.
+    if (top_pass) {
 #pragma unroll
-    for (int i = 0; i < kSortItems; ++i) {
-      const long long idx = base + i * 32 + lane;
-      const uint32_t dg = (key[i] >> shift) & dmask;
-      rank[i] = __match_any_sync(0xffffffffu, idx < n ? dg : 0x10000u + lane);
+      for (int i = 0; i < kSortItems; ++i) {
+        const long long idx = base + i * 32 + lane;
+        const uint32_t dg = (key[i] >> shift) & dmask;
+        uint32_t peers = __ballot_sync(0xffffffffu, idx < n);
+        if (!__all_sync(0xffffffffu, dg == __shfl_sync(0xffffffffu, dg, 0))) peers = digit_peers<RB>(dg, peers);
+        rank[i] = idx < n ? peers : (1u << lane);
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < kSortItems; ++i) {
+        const long long idx = base + i * 32 + lane;
+        const uint32_t dg = (key[i] >> shift) & dmask;
+        const uint32_t peers = digit_peers<RB>(dg, __ballot_sync(0xffffffffu, idx < n));   // every lane votes
+        rank[i] = idx < n ? peers : (1u << lane);
+      }
     }
 #pragma unroll
     for (int i = 0; i < kSortItems; ++i) {

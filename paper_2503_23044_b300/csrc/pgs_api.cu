@@ -432,13 +432,15 @@ pgs_status run_project(pgs_scene* s, const BatchDev& b, DecodeOut dec, bool proj
     k_rows_total<<<1, 1, 0, st>>>(s->d_tot, s->cap_rows, s->d_cnt, s->d_cnt + 1, s->d_flags);
     const int prec = s->d.params.decode_precision;
     if (prec == PGS_DECODE_BF16 || prec == PGS_DECODE_BF16_1PASS) {
+      // the decoded outputs pass through the decoder-backward row scratch (free until pgs_backward)
       PGS_CUDA(launch_decode_project_tc(prec == PGS_DECODE_BF16, b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
-                                        project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags, st));
+                                        s->sc_dZ, project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags,
+                                        st));
     } else {
       k_decode_project<<<ns * 4, 256, 0, st>>>(b, s->an, s->mlp, s->rows, s->d_cnt, s->cap_rows,
                                               project ? s->rec : nullptr, s->counts, s->keys_a, dec, s->d_flags);
     }
-    s->launches += 5 + kScanLaunches;
+    s->launches += 5 + kScanLaunches + ((prec == PGS_DECODE_BF16 || prec == PGS_DECODE_BF16_1PASS) ? 1 : 0);
   }
   prof_mark(s, PGS_STAGE_PROJECT, 1, st);
   PGS_CUDA(cudaGetLastError());

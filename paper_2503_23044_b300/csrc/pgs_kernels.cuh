@@ -64,12 +64,13 @@ __global__ void k_decode_project(const __grid_constant__ BatchDev b, pgs_anchor_
                                  uint32_t* counts, uint32_t* keys, DecodeOut dec, uint32_t* err);
 
 // k_decode_tc.cu: the tensor-core decoder + projection; split = true is the production precision (layer 1 and
-// the opacity / scale / rotation heads FP32-accurate, colour heads one BF16 pass), false the one-pass study form
+// the opacity / scale / rotation heads FP32-accurate, colour heads one BF16 pass), false the one-pass study form.
+// zbuf: the decoded outputs pass through it (the row scratch layout, kOut features, at least sc_rows(cap) rows).
 size_t decode_tc_smem_bytes();
 cudaError_t launch_decode_project_tc(bool split, const BatchDev& b, const pgs_anchor_ptrs& A, const pgs_mlp_ptrs& W,
-                                     const uint32_t* rows, const long long* n_rows, long long cap, float4* rec,
-                                     uint32_t* counts, uint32_t* keys, const DecodeOut& dec, uint32_t* err,
-                                     cudaStream_t st);
+                                     const uint32_t* rows, const long long* n_rows, long long cap, float* zbuf,
+                                     float4* rec, uint32_t* counts, uint32_t* keys, const DecodeOut& dec,
+                                     uint32_t* err, cudaStream_t st);
 
 // k_sort.cu
 void launch_exclusive_scan(const uint32_t* in, const uint32_t* index, uint32_t* out, unsigned long long* total,
