@@ -16,6 +16,8 @@
 // 3. Filter: D~_f(p) = D~_p(p) where E(p) <= tau_d, or where no neighbour could
 //    check p; 0 where E(p) > tau_d or the prior is missing.  The mask is the
 //    depth L1 mask of the loss.
+#include <algorithm>
+
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
 
@@ -112,19 +114,44 @@ __global__ void k_prior_fit_final(const float* __restrict__ partials, int nb, in
   }
 }
 
+// Bilinear footprint of continuous pixel coordinates (x, y) in view v: the
+// address of the top-left sample and the weights; false outside the frame.
+// prior_bilinear split in two so that a thread can issue the loads of every
+// neighbour view before it uses any of them.
+__device__ __forceinline__ bool prior_footprint(const ViewDev& v, float x, float y, long long& at, float& au,
+                                                float& aw) {
+  const float u = x - 0.5f, w = y - 0.5f;
+  const float fu = floorf(u), fw = floorf(w);
+  if (!(fu >= 0.f && fw >= 0.f && fu + 1.f <= (float)(v.W - 1) && fw + 1.f <= (float)(v.H - 1))) return false;
+  at = v.pix_off + (long long)(int)fw * v.W + (int)fu;
+  au = u - fu;
+  aw = w - fw;
+  return true;
+}
+
+// One thread per pixel at a time (grid-stride).  The pixel's own pseudo depth is
+// loaded one iteration ahead, and the k neighbour views are taken in two phases
+// (project and issue the four loads of every neighbour, then finish the round
+// trips), so the gathers of a pixel are in flight together; the arithmetic of
+// each neighbour and the order of the minimum are those of the definition above.
+// K = pa.k, the number of neighbour views (0..kPriorMaxK), fixed per launch.
+template <int K>
 __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ BatchDev b, PriorArgs pa,
                                                       const float* __restrict__ dp,
                                                       const float* __restrict__ scale_shift,
                                                       float* __restrict__ prior_out, float* __restrict__ mask_out,
                                                       float* __restrict__ err_out) {
   int vi = 0;   // threads walk increasing pixel indices, so the view only moves forward
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < b.total_pixels;
-       p += (long long)gridDim.x * blockDim.x) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  float raw_next = p < b.total_pixels ? __ldg(dp + p) : 0.f;
+  for (; p < b.total_pixels; p += stride) {
+    const float raw = raw_next;
+    raw_next = p + stride < b.total_pixels ? __ldg(dp + p + stride) : 0.f;
     while (vi + 1 < b.n_views && p >= b.v[vi + 1].pix_off) ++vi;
     const ViewDev& va = b.v[vi];
     const unsigned l = (unsigned)(p - va.pix_off);
     const int py = (int)(l / (unsigned)va.W), px = (int)(l - (unsigned)py * (unsigned)va.W);
-    const float raw = __ldg(dp + p);
     const float d = fmaf(scale_shift[2 * vi], raw, scale_shift[2 * vi + 1]);
     float keep_d = 0.f, keep = 0.f, E = -1.f;
     if (raw > 0.f && d > 0.f) {
@@ -132,9 +159,14 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
       const float ca[3] = {d * (ux - va.cx) * rcp_approx(va.fx), d * (uy - va.cy) * rcp_approx(va.fy), d};
       float xw[3];
       to_world(va, ca, xw);
-      float best = 3.4e38f;
-      bool checked = false;
-      for (int i = 0; i < pa.k; ++i) {
+      // phase 1: every neighbour's projection and its four samples
+      float qx[K + 1], qy[K + 1], au[K + 1], aw[K + 1], sm[K + 1][4];
+      bool ok[K + 1];
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        ok[i] = false;
+        qx[i] = qy[i] = au[i] = aw[i] = 0.f;
+        sm[i][0] = sm[i][1] = sm[i][2] = sm[i][3] = 0.f;
         const int nb = pa.nbr[vi][i];
         if (nb < 0) continue;
         const ViewDev& vb = b.v[nb];
@@ -142,12 +174,29 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
         to_cam(vb, xw, cb);
         if (!(cb[2] > b.p.near_plane)) continue;
         const float izb = rcp_approx(cb[2]);
-        const float qx = fmaf(vb.fx * cb[0], izb, vb.cx), qy = fmaf(vb.fy * cb[1], izb, vb.cy);
-        float rb;
-        if (!prior_bilinear(dp, vb, qx, qy, rb)) continue;
+        qx[i] = fmaf(vb.fx * cb[0], izb, vb.cx);
+        qy[i] = fmaf(vb.fy * cb[1], izb, vb.cy);
+        long long at;
+        if (!prior_footprint(vb, qx[i], qy[i], at, au[i], aw[i])) continue;
+        const float* r0 = dp + at;
+        sm[i][0] = __ldg(r0); sm[i][1] = __ldg(r0 + 1); sm[i][2] = __ldg(r0 + vb.W); sm[i][3] = __ldg(r0 + vb.W + 1);
+        ok[i] = true;
+      }
+      // phase 2: the round trips back into view a, in neighbour order
+      float best = 3.4e38f;
+      bool checked = false;
+#pragma unroll
+      for (int i = 0; i < K; ++i) {
+        if (!ok[i]) continue;
+        const float a = sm[i][0], bb = sm[i][1], c = sm[i][2], dd = sm[i][3];
+        if (!(a > 0.f && bb > 0.f && c > 0.f && dd > 0.f)) continue;
+        const float top = fmaf(au[i], bb - a, a), bot = fmaf(au[i], dd - c, c);
+        const float rb = fmaf(aw[i], bot - top, top);
+        const int nb = pa.nbr[vi][i];
+        const ViewDev& vb = b.v[nb];
         const float db = fmaf(scale_shift[2 * nb], rb, scale_shift[2 * nb + 1]);
         if (!(db > 0.f)) continue;
-        const float cb2[3] = {db * (qx - vb.cx) * rcp_approx(vb.fx), db * (qy - vb.cy) * rcp_approx(vb.fy), db};
+        const float cb2[3] = {db * (qx[i] - vb.cx) * rcp_approx(vb.fx), db * (qy[i] - vb.cy) * rcp_approx(vb.fy), db};
         float xw2[3], ca2[3];
         to_world(vb, cb2, xw2);
         to_cam(va, xw2, ca2);
@@ -174,7 +223,18 @@ void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp
     k_prior_fit_partial<<<g, 256, 0, st>>>(b, dp, pts, n_pts, pass, means, partials);
     k_prior_fit_final<<<1, kMaxViews, 0, st>>>(partials, kPriorBlocks, b.n_views, pass, means, scale_shift);
   }
-  k_prior_filter<<<num_sms * 8, 256, 0, st>>>(b, pa, dp, scale_shift, prior_out, mask_out, err_out);
+  // one resident wave of the variant for this neighbour count
+  auto filter = [&](auto kernel) {
+    const int fg = std::max(1, resident_ctas_per_sm(reinterpret_cast<const void*>(kernel), 256)) * num_sms;
+    kernel<<<fg, 256, 0, st>>>(b, pa, dp, scale_shift, prior_out, mask_out, err_out);
+  };
+  switch (pa.k) {
+    case 0: filter(k_prior_filter<0>); break;
+    case 1: filter(k_prior_filter<1>); break;
+    case 2: filter(k_prior_filter<2>); break;
+    case 3: filter(k_prior_filter<3>); break;
+    default: filter(k_prior_filter<kPriorMaxK>);
+  }
 }
 
 }  // namespace pgs

@@ -158,6 +158,7 @@ SortScratch sort_scratch_layout(void* base, long long n_max, int radix_bits_max)
   return s;
 }
 
+constexpr int kHistLoads = 8;
 template <int RB>
 __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ keys, const long long* __restrict__ d_n,
                                                    long long n_max, int bit_lo, int bit_hi, int n_pass,
@@ -168,12 +169,21 @@ __global__ void __launch_bounds__(256) k_sort_hist(const uint32_t* __restrict__ 
   for (int i = threadIdx.x; i < 4 * kRadix; i += blockDim.x) s_h[i] = 0;
   __syncthreads();
   const long long n = max(0ll, min(*d_n, n_max));
-  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
-    const uint32_t key = keys[k];
-    for (int p = 0; p < n_pass; ++p) {
-      const int sh = bit_lo + RB * p;
-      const uint32_t i = p * R + ((key >> sh) & digit_mask(sh, bit_hi, RB));
-      if (in_bounds(i < 4u * kRadix, err)) atomicAdd(&s_h[i], 1u);
+  // kHistLoads keys per thread are loaded before any of them is counted, so each thread
+  // keeps that many loads in flight (counts are integers: the order of the adds is free)
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k0 = blockIdx.x * (long long)blockDim.x + threadIdx.x; k0 < n; k0 += kHistLoads * stride) {
+    uint32_t kk[kHistLoads];
+#pragma unroll
+    for (int u = 0; u < kHistLoads; ++u) kk[u] = k0 + u * stride < n ? keys[k0 + u * stride] : 0u;
+#pragma unroll
+    for (int u = 0; u < kHistLoads; ++u) {
+      if (k0 + u * stride >= n) break;
+      for (int p = 0; p < n_pass; ++p) {
+        const int sh = bit_lo + RB * p;
+        const uint32_t i = p * R + ((kk[u] >> sh) & digit_mask(sh, bit_hi, RB));
+        if (in_bounds(i < 4u * kRadix, err)) atomicAdd(&s_h[i], 1u);
+      }
     }
   }
   // clear the look-back status of the first pass for the live tiles
