@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_HERE, "libpgs_checked.so" if os.environ.get("PGS_LIB") 
 (PGS_OK, PGS_ERR_INVALID_ARG, PGS_ERR_CAPACITY, PGS_ERR_TIMEOUT, PGS_ERR_NONFINITE, PGS_ERR_CUDA, PGS_ERR_UNSUPPORTED,
  PGS_ERR_BOUNDS) = range(8)
 MODE_EXPLICIT, MODE_ANCHOR = 0, 1
+N_OFFSETS, FEAT_DIM, HIDDEN, OUT_DIM = 10, 32, 32, 110   # PGS_N_OFFSETS, PGS_FEAT_DIM, PGS_HIDDEN, PGS_OUT_DIM
 DECODE_FP32, DECODE_BF16, DECODE_BF16_1PASS = 0, 1, 2
 MAX_VIEWS = 32
 
@@ -28,6 +29,14 @@ class PGSError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"pgs status {status}: {msg}")
         self.status = status
+
+
+class ArgumentError(PGSError, ValueError):
+    """An argument the binding refuses before any device work (status PGS_ERR_INVALID_ARG): the
+    C entry points see bare pointers, so sizes and element types are checked here."""
+
+    def __init__(self, msg: str):
+        super().__init__(PGS_ERR_INVALID_ARG, msg)
 
 
 _lib = None
@@ -185,15 +194,46 @@ def _ptr(t: Optional[torch.Tensor]) -> Optional[int]:
     if t is None:
         return None
     if not t.is_cuda:
-        raise ValueError("tensor must live on a CUDA device")
+        raise ArgumentError("tensor must live on a CUDA device")
     if not t.is_contiguous():
-        raise ValueError("tensor must be contiguous")
+        raise ArgumentError("tensor must be contiguous")
     return t.data_ptr()
 
 
 def _stream(stream: Optional[torch.cuda.Stream]) -> int:
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+# The C entry points receive bare device pointers and cannot see how large a
+# buffer is: a tensor of the wrong length or element type would be read or
+# written out of range on the device.  The binding therefore checks every
+# tensor it passes against the size the call implies and raises ValueError
+# before any device work.
+def _expect(t: Optional[torch.Tensor], numel: int, name: str, dtype=torch.float32, optional: bool = False) -> None:
+    if t is None:
+        if optional:
+            return
+        raise ArgumentError(f"{name} is required")
+    if t.dtype != dtype:
+        raise ArgumentError(f"{name} must be {dtype} (got {t.dtype})")
+    if t.numel() != numel:
+        raise ArgumentError(f"{name} must have {numel} elements (got {t.numel()})")
+
+
+def check_anchor_tensors(n_anchors: int, in_dim: int, x, level, log_l, offsets, feat, W1, b1, W2, b2) -> None:
+    """Shapes of pgs_anchor_ptrs / pgs_mlp_ptrs for a scene of n_anchors anchors (include/pgs.h)."""
+    N = n_anchors
+    _expect(x, 3 * N, "x"); _expect(level, N, "level", torch.int32); _expect(log_l, 3 * N, "log_l")
+    _expect(offsets, N * N_OFFSETS * 3, "offsets"); _expect(feat, N * FEAT_DIM, "feat")
+    _expect(W1, HIDDEN * in_dim, "W1"); _expect(b1, HIDDEN, "b1")
+    _expect(W2, OUT_DIM * HIDDEN, "W2"); _expect(b2, OUT_DIM, "b2")
+
+
+def check_explicit_tensors(n: int, means, log_scales, quats, opacity_logits, colors) -> None:
+    """Shapes of pgs_explicit_ptrs for a scene of n explicit Gaussians (include/pgs.h)."""
+    _expect(means, 3 * n, "means"); _expect(log_scales, 3 * n, "log_scales"); _expect(quats, 4 * n, "quats")
+    _expect(opacity_logits, n, "opacity_logits"); _expect(colors, 3 * n, "colors")
 
 
 def default_params(**kw) -> RenderParams:
@@ -253,6 +293,17 @@ class Images:
         return Images(f(3 * n), f(n), f(3 * n), f(n), f(n), i(n), i(n) if stats else None, i(n) if stats else None,
                       off, [(int(c.height), int(c.width)) for c in cams])
 
+    def check(self, cams) -> None:
+        """Raise ValueError unless these buffers are laid out for the arena of ``cams``."""
+        if list(self.offsets) != arena_offsets(cams):
+            raise ArgumentError("images were allocated for another set of views (arena offsets differ)")
+        n = self.offsets[-1]
+        for k, m in (("rgb", 3 * n), ("depth", n), ("normal", 3 * n), ("dist", n), ("t_final", n)):
+            _expect(getattr(self, k), m, f"images.{k}")
+        _expect(self.last, n, "images.last", torch.int32)
+        _expect(self.n_contrib, n, "images.n_contrib", torch.int32, optional=True)
+        _expect(self.n_eval, n, "images.n_eval", torch.int32, optional=True)
+
     def without_stats(self) -> "Images":
         """The same buffers with the diagnostic counts switched off."""
         return dataclasses.replace(self, n_contrib=None, n_eval=None)
@@ -288,6 +339,10 @@ class ImageGrads:
         cat = lambda k: torch.cat([v[k].reshape(-1) for v in views]).to(device, torch.float32).contiguous()
         return ImageGrads(cat("rgb"), cat("depth"), cat("normal"))
 
+    def check(self, n_pix: int) -> None:
+        _expect(self.rgb, 3 * n_pix, "grads.rgb"); _expect(self.depth, n_pix, "grads.depth")
+        _expect(self.normal, 3 * n_pix, "grads.normal")
+
     def ptrs(self) -> ImageGradPtrs:
         return ImageGradPtrs(_ptr(self.rgb), _ptr(self.depth), _ptr(self.normal))
 
@@ -302,6 +357,10 @@ class Targets:
     def from_views(views: Sequence[dict], device="cuda") -> "Targets":
         cat = lambda k: torch.cat([v[k].reshape(-1) for v in views]).to(device, torch.float32).contiguous()
         return Targets(cat("rgb"), cat("prior"), cat("mask"))
+
+    def check(self, n_pix: int) -> None:
+        _expect(self.rgb, 3 * n_pix, "targets.rgb"); _expect(self.prior, n_pix, "targets.prior")
+        _expect(self.mask, n_pix, "targets.mask")
 
     def ptrs(self) -> TargetPtrs:
         return TargetPtrs(_ptr(self.rgb), _ptr(self.prior), _ptr(self.mask))
@@ -320,6 +379,17 @@ class Scene:
         check(lib().pgs_scene_create(C.byref(self.desc), C.byref(h)))
         self.handle = h
         self._keep = []
+        self._grad_numel: Dict[str, int] = {}
+
+    def _param_grad_ptrs(self, param_grads: Dict[str, torch.Tensor]) -> ParamGradPtrs:
+        """Gradient buffers are accumulated into: each one must match its bound parameter's size."""
+        for n, t in param_grads.items():
+            if t is None:
+                continue
+            if n not in self._grad_numel:
+                raise ArgumentError(f"param_grads[{n!r}]: no such parameter is bound to this scene")
+            _expect(t, self._grad_numel[n], f"param_grads[{n!r}]")
+        return ParamGradPtrs(*[_ptr(param_grads.get(n)) for n in PARAM_GRAD_FIELDS])
 
     def close(self):
         if getattr(self, "handle", None):
@@ -333,18 +403,26 @@ class Scene:
             pass
 
     def bind_explicit(self, means, log_scales, quats, opacity_logits, colors):
+        check_explicit_tensors(self.desc.n_primitives, means, log_scales, quats, opacity_logits, colors)
         ts = [t.contiguous() for t in (means, log_scales, quats, opacity_logits, colors)]
         self._keep = ts
+        self._grad_numel = dict(zip(("means", "log_scales", "quats", "opacity_logits", "colors"),
+                                    (t.numel() for t in ts)))
         check(lib().pgs_scene_bind_explicit(self.handle, C.byref(ExplicitPtrs(*[_ptr(t) for t in ts]))))
 
     def bind_anchors(self, x, level, log_l, offsets, feat, W1, b1, W2, b2):
+        check_anchor_tensors(self.desc.n_primitives, self.desc.params.in_dim, x, level, log_l, offsets, feat, W1, b1,
+                             W2, b2)
         ts = [t.contiguous() for t in (x, level, log_l, offsets, feat, W1, b1, W2, b2)]
         self._keep = ts
+        self._grad_numel = {n: t.numel() for n, t in zip(("x", "level", "log_l", "offsets", "feat", "W1", "b1", "W2",
+                                                            "b2"), ts) if n != "level"}
         check(lib().pgs_scene_bind_anchors(self.handle, C.byref(AnchorPtrs(*[_ptr(t) for t in ts[:5]])),
                                            C.byref(MlpPtrs(*[_ptr(t) for t in ts[5:]]))))
 
     def render(self, cams, images: Optional[Images] = None, stream=None, packed=None) -> Images:
         images = images if images is not None else Images.empty(cams)
+        images.check(cams)
         cc = packed if packed is not None else pack_cameras(cams)
         check(lib().pgs_render_batch(self.handle, cc, len(cams), C.byref(images.ptrs()), _stream(stream)))
         return images
@@ -354,6 +432,11 @@ class Scene:
         n = images.offsets[-1]
         loss = loss if loss is not None else torch.zeros(4, device=images.rgb.device)
         grads = grads if grads is not None else ImageGrads.empty(n, images.rgb.device)
+        images.check(cams)
+        targets.check(n)
+        grads.check(n)
+        if loss.dtype != torch.float32 or loss.numel() < 4:
+            raise ArgumentError("loss must be float32 with at least 4 elements (total, rgb, depth, normal)")
         cc = packed if packed is not None else pack_cameras(cams)
         check(lib().pgs_loss_grad(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(targets.ptrs()),
                                   C.byref(LossParams(lambda_depth, lambda_normal)), _ptr(loss), C.byref(grads.ptrs()),
@@ -362,7 +445,9 @@ class Scene:
 
     def backward(self, cams, images: Images, grads: ImageGrads, param_grads: Dict[str, torch.Tensor], stream=None,
                  packed=None):
-        pg = ParamGradPtrs(*[_ptr(param_grads.get(n)) for n in PARAM_GRAD_FIELDS])
+        images.check(cams)
+        grads.check(images.offsets[-1])
+        pg = self._param_grad_ptrs(param_grads)
         cc = packed if packed is not None else pack_cameras(cams)
         check(lib().pgs_backward(self.handle, cc, len(cams), C.byref(images.ptrs()), C.byref(grads.ptrs()),
                                  C.byref(pg), _stream(stream)))
@@ -371,7 +456,9 @@ class Scene:
                  stream=None, packed=None) -> List[dict]:
         """Pick tile shape and forward shared-memory batch by timing (pgs_autotune); returns the
         timed combinations (one entry with ms = -1 when the choice came from the cache)."""
-        pg = ParamGradPtrs(*[_ptr(param_grads.get(n)) for n in PARAM_GRAD_FIELDS])
+        images.check(cams)
+        grads.check(images.offsets[-1])
+        pg = self._param_grad_ptrs(param_grads)
         cc = packed if packed is not None else pack_cameras(cams)
         out = (TuneEntry * 16)()
         n = C.c_int(0)
@@ -385,7 +472,10 @@ class Scene:
         """Enhanced depth prior (pgs_filter_depth_prior): pseudo depth in the arena layout and world
         points [n, 3] -> dict(prior, mask, scale_shift [views, 2], err).  `out` may supply the
         prior / mask / scale_shift buffers (e.g. a Targets' prior and mask)."""
-        n = pseudo.numel()
+        n = arena_offsets(cams)[-1]
+        _expect(pseudo, n, "pseudo")
+        if points.dim() != 2 or points.shape[-1] != 3 or points.dtype != torch.float32:
+            raise ArgumentError(f"points must be float32 [n, 3] (got {points.dtype} {tuple(points.shape)})")
         given = out or {}
         out = dict(prior=given.get("prior", None), mask=given.get("mask", None),
                    scale_shift=given.get("scale_shift", None), err=None)
@@ -397,6 +487,8 @@ class Scene:
             out["scale_shift"] = torch.empty(len(cams), 2, device=pseudo.device)
         if with_error:
             out["err"] = torch.empty(n, device=pseudo.device)
+        _expect(out["prior"], n, "out['prior']"); _expect(out["mask"], n, "out['mask']")
+        _expect(out["scale_shift"], 2 * len(cams), "out['scale_shift']")
         cc = packed if packed is not None else pack_cameras(cams)
         pts = points.contiguous()
         pp = PriorParams(tau_d, k_neighbors)
@@ -420,6 +512,16 @@ class Scene:
             ncc_out = torch.empty(max(1, n_pairs * n_per), device=images.rgb.device)
         if loss is None:
             loss = torch.zeros(2, device=images.rgb.device)
+        images.check(cams)
+        grads.check(images.offsets[-1])
+        if centers.numel() and (centers.dtype not in (torch.int32, torch.uint32) or
+                                centers.numel() != n_pairs * n_per):
+            raise ArgumentError(f"centers must be int32/uint32 [{n_pairs}, N] (got {centers.dtype} "
+                             f"{tuple(centers.shape)})")
+        if ncc_out.dtype != torch.float32 or ncc_out.numel() < max(1, n_pairs * n_per):
+            raise ArgumentError(f"ncc_out must be float32 with at least {max(1, n_pairs * n_per)} elements")
+        if loss.dtype != torch.float32 or loss.numel() < 2:
+            raise ArgumentError("loss must be float32 with at least 2 elements")
         npar = NccParams(lambda_ncc, eps, 1 if geometric else 0)
         check(lib().pgs_ncc_loss_grad(self.handle, cc, len(cams), C.byref(images.ptrs()),
                                       _ptr(centers) if centers.numel() else None, n_per, C.byref(npar),
@@ -434,6 +536,12 @@ class Scene:
         vol = TsdfVolume((C.c_float * 3)(*volume["origin"]), volume["voxel"], (C.c_int32 * 3)(*volume["dims"]),
                          volume["trunc"])
         color = volume.get("color") if rgb is not None else None
+        n = arena_offsets(cams)[-1]
+        nv = int(volume["dims"][0]) * int(volume["dims"][1]) * int(volume["dims"][2])
+        _expect(depth, n, "depth"); _expect(rgb, 3 * n, "rgb", optional=True)
+        _expect(volume["tsdf"], nv, "volume['tsdf']"); _expect(volume["weight"], nv, "volume['weight']")
+        if rgb is not None:
+            _expect(color, 3 * nv, "volume['color']")
         check(lib().pgs_tsdf_integrate(self.handle, cc, len(cams), _ptr(depth), _ptr(rgb), C.byref(vol),
                                        _ptr(volume["tsdf"]), _ptr(volume["weight"]), _ptr(color), _stream(stream)))
         return volume
@@ -497,16 +605,16 @@ def _check_sort_operands(keys: torch.Tensor, vals: torch.Tensor) -> None:
     checks what they cannot: equal element counts, 4-byte elements,
     contiguous CUDA tensors on the current device.  Raises ValueError."""
     if keys.numel() != vals.numel():
-        raise ValueError(f"keys ({keys.numel()}) and values ({vals.numel()}) differ in length")
+        raise ArgumentError(f"keys ({keys.numel()}) and values ({vals.numel()}) differ in length")
     if keys.element_size() != 4 or vals.element_size() != 4:
-        raise ValueError(f"keys and values need 4-byte elements (got {keys.dtype}, {vals.dtype})")
+        raise ArgumentError(f"keys and values need 4-byte elements (got {keys.dtype}, {vals.dtype})")
     if not (keys.is_contiguous() and vals.is_contiguous()):
-        raise ValueError("keys and values must be contiguous")
+        raise ArgumentError("keys and values must be contiguous")
     if keys.device.type != "cuda" or vals.device.type != "cuda":
-        raise ValueError(f"keys and values must be CUDA tensors (got {keys.device}, {vals.device})")
+        raise ArgumentError(f"keys and values must be CUDA tensors (got {keys.device}, {vals.device})")
     cur = torch.cuda.current_device()
     if keys.device.index != cur or vals.device.index != cur:
-        raise ValueError(f"keys ({keys.device}) and values ({vals.device}) must sit on the current device cuda:{cur}")
+        raise ArgumentError(f"keys ({keys.device}) and values ({vals.device}) must sit on the current device cuda:{cur}")
 
 
 def sort_pairs(keys: torch.Tensor, vals: torch.Tensor, bit_lo: int = 0, bit_hi: int = 32):
