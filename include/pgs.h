@@ -53,7 +53,7 @@ enum pgs_status_code {
   PGS_ERR_TIMEOUT = 3,       /* a bounded device-side wait (sort look-back) ran out */
   PGS_ERR_NONFINITE = 4,     /* non-finite value met in a parameter, a loss or a gradient */
   PGS_ERR_CUDA = 5,          /* a CUDA runtime call failed */
-  PGS_ERR_UNSUPPORTED = 6,   /* valid request this build does not handle */
+  PGS_ERR_UNSUPPORTED = 6,   /* valid request the library does not handle */
   PGS_ERR_BOUNDS = 7         /* an index failed a bounds check (bounds-checked build only; the access was skipped) */
 };
 
