@@ -249,7 +249,10 @@ pgs_status pgs_get_stats(pgs_scene* s, pgs_stats* out, cudaStream_t stream);
  * events on the launching stream (recorded as external event nodes when the
  * stream is being captured into a graph).  pgs_get_stage_times waits for
  * those events and writes the most recent duration of each stage in ms (-1
- * if it did not run) for the first n of PGS_N_STAGES stages. */
+ * if it did not run) for the first n of PGS_N_STAGES stages.  Profiling also
+ * opens an NVTX range named after the stage ("pgs:blend_bwd", ...) around the
+ * host-side enqueue of each stage, for timeline tools; with no NVTX tool
+ * attached those calls do nothing. */
 enum pgs_stage {
   PGS_STAGE_PROJECT = 0,      /* cull + decode + projection + tile counts */
   PGS_STAGE_DEPTH_SORT = 1,   /* radix sort of the Gaussian-views by depth */

@@ -12,6 +12,8 @@
 #include <tuple>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "pgs_internal.cuh"
 #include "pgs_kernels.cuh"
 
@@ -167,8 +169,15 @@ struct pgs_scene {
 
 namespace {
 // stage brackets: CUDA events on the launching stream (external event nodes when captured)
+// NVTX range names of the stages (pgs_stage order)
+const char* const kStageRange[PGS_N_STAGES] = {"pgs:project", "pgs:depth_sort", "pgs:bin", "pgs:tile_sort",
+                                               "pgs:blend_fwd", "pgs:loss", "pgs:blend_bwd", "pgs:project_bwd",
+                                               "pgs:wgrad", "pgs:prior", "pgs:ncc", "pgs:tsdf"};
+
 void prof_mark(pgs_scene* s, int stage, int which, cudaStream_t st) {
   if (!s->prof) return;
+  if (which == 0) nvtxRangePushA(kStageRange[stage]);
+  else nvtxRangePop();
   cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
   cudaStreamIsCapturing(st, &cs);
   cudaEventRecordWithFlags(s->ev[stage][which], st, cs == cudaStreamCaptureStatusActive ? cudaEventRecordExternal : 0);
