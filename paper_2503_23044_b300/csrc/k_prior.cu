@@ -141,6 +141,21 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
                                                       const float* __restrict__ scale_shift,
                                                       float* __restrict__ prior_out, float* __restrict__ mask_out,
                                                       float* __restrict__ err_out) {
+  // the batch's view parameters, scale/shift pairs and neighbour lists, read at data-dependent
+  // indices for every pixel, are copied once per CTA into shared memory
+  __shared__ ViewDev s_v[kMaxViews];
+  __shared__ float s_ss[2 * kMaxViews];
+  __shared__ int s_nbr[kMaxViews][K + 1];
+  {
+    const int nw = b.n_views * (int)(sizeof(ViewDev) / sizeof(uint32_t));
+    const uint32_t* src = reinterpret_cast<const uint32_t*>(&b.v[0]);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(&s_v[0]);
+    for (int i = threadIdx.x; i < nw; i += blockDim.x) dst[i] = src[i];
+    for (int i = threadIdx.x; i < 2 * b.n_views; i += blockDim.x) s_ss[i] = scale_shift[i];
+    if constexpr (K > 0)
+      for (int i = threadIdx.x; i < b.n_views * K; i += blockDim.x) s_nbr[i / K][i % K] = pa.nbr[i / K][i % K];
+  }
+  __syncthreads();
   int vi = 0;   // threads walk increasing pixel indices, so the view only moves forward
   const long long stride = (long long)gridDim.x * blockDim.x;
   long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -148,11 +163,11 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
   for (; p < b.total_pixels; p += stride) {
     const float raw = raw_next;
     raw_next = p + stride < b.total_pixels ? __ldg(dp + p + stride) : 0.f;
-    while (vi + 1 < b.n_views && p >= b.v[vi + 1].pix_off) ++vi;
-    const ViewDev& va = b.v[vi];
+    while (vi + 1 < b.n_views && p >= s_v[vi + 1].pix_off) ++vi;
+    const ViewDev& va = s_v[vi];
     const unsigned l = (unsigned)(p - va.pix_off);
     const int py = (int)(l / (unsigned)va.W), px = (int)(l - (unsigned)py * (unsigned)va.W);
-    const float d = fmaf(scale_shift[2 * vi], raw, scale_shift[2 * vi + 1]);
+    const float d = fmaf(s_ss[2 * vi], raw, s_ss[2 * vi + 1]);
     float keep_d = 0.f, keep = 0.f, E = -1.f;
     if (raw > 0.f && d > 0.f) {
       const float ux = (float)px + 0.5f, uy = (float)py + 0.5f;
@@ -167,9 +182,9 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
         ok[i] = false;
         qx[i] = qy[i] = au[i] = aw[i] = 0.f;
         sm[i][0] = sm[i][1] = sm[i][2] = sm[i][3] = 0.f;
-        const int nb = pa.nbr[vi][i];
+        const int nb = s_nbr[vi][i];
         if (nb < 0) continue;
-        const ViewDev& vb = b.v[nb];
+        const ViewDev& vb = s_v[nb];
         float cb[3];
         to_cam(vb, xw, cb);
         if (!(cb[2] > b.p.near_plane)) continue;
@@ -192,9 +207,9 @@ __global__ void __launch_bounds__(256) k_prior_filter(const __grid_constant__ Ba
         if (!(a > 0.f && bb > 0.f && c > 0.f && dd > 0.f)) continue;
         const float top = fmaf(au[i], bb - a, a), bot = fmaf(au[i], dd - c, c);
         const float rb = fmaf(aw[i], bot - top, top);
-        const int nb = pa.nbr[vi][i];
-        const ViewDev& vb = b.v[nb];
-        const float db = fmaf(scale_shift[2 * nb], rb, scale_shift[2 * nb + 1]);
+        const int nb = s_nbr[vi][i];
+        const ViewDev& vb = s_v[nb];
+        const float db = fmaf(s_ss[2 * nb], rb, s_ss[2 * nb + 1]);
         if (!(db > 0.f)) continue;
         const float cb2[3] = {db * (qx[i] - vb.cx) * rcp_approx(vb.fx), db * (qy[i] - vb.cy) * rcp_approx(vb.fy), db};
         float xw2[3], ca2[3];
