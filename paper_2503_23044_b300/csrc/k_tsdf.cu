@@ -26,9 +26,27 @@ constexpr int kTsdfGroup = 4;   // views projected (and their pixels fetched) to
 constexpr int kBrick = 8;       // voxels per brick edge (a brick is 512 consecutive threads)
 static_assert(kBrick * kBrick * kBrick == 512, "the thread index splits as brick << 9 | voxel in brick");
 
+// Depth and colour of every pixel interleaved as one 16-byte record (D, r, g, b): a
+// voxel-view sample then reads one 32-byte sector instead of four (the depth plane
+// and three colour planes), since voxels sit several pixels apart in the views.
+__global__ void __launch_bounds__(256) k_tsdf_pack(const __grid_constant__ BatchDev b, const float* __restrict__ depth,
+                                                   const float* __restrict__ rgb, float4* __restrict__ packed) {
+  int vi = 0;   // threads walk increasing pixel indices, so the view only moves forward
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < b.total_pixels;
+       p += (long long)gridDim.x * blockDim.x) {
+    while (vi + 1 < b.n_views && p >= b.v[vi + 1].pix_off) ++vi;
+    const ViewDev& w = b.v[vi];
+    const long long HW = (long long)w.W * w.H;
+    const long long p3 = 2 * w.pix_off + p;
+    packed[p] = make_float4(__ldg(depth + p), __ldg(rgb + p3), __ldg(rgb + p3 + HW), __ldg(rgb + p3 + 2 * HW));
+  }
+}
+
+// packed: the maps interleaved by k_tsdf_pack (with colour), or null to read the planes
 __global__ void __launch_bounds__(256) k_tsdf_integrate(const __grid_constant__ BatchDev b, TsdfArgs a,
                                                         const float* __restrict__ depth,
-                                                        const float* __restrict__ rgb, float* __restrict__ tsdf,
+                                                        const float* __restrict__ rgb,
+                                                        const float4* __restrict__ packed, float* __restrict__ tsdf,
                                                         float* __restrict__ weight, float* __restrict__ color) {
   const long long nxy = (long long)a.dims[0] * a.dims[1];
   const int nbx = (a.dims[0] + kBrick - 1) / kBrick, nby = (a.dims[1] + kBrick - 1) / kBrick;
@@ -76,13 +94,21 @@ __global__ void __launch_bounds__(256) k_tsdf_integrate(const __grid_constant__ 
         if (!(fu >= 0.f && fv >= 0.f && fu <= (float)(w.W - 1) && fv <= (float)(w.H - 1))) continue;
         const long long p = w.pix_off + (long long)((int)fv * w.W + (int)fu);
         zc[t] = z;
-        dd[t] = __ldg(depth + p);
-        if (color) {
-          const long long HW = (long long)w.W * w.H;
-          const long long p3 = 2 * w.pix_off + p;
-          cc[t][0] = __ldg(rgb + p3);
-          cc[t][1] = __ldg(rgb + p3 + HW);
-          cc[t][2] = __ldg(rgb + p3 + 2 * HW);
+        if (packed) {
+          const float4 q = __ldg(packed + p);
+          dd[t] = q.x;
+          cc[t][0] = q.y;
+          cc[t][1] = q.z;
+          cc[t][2] = q.w;
+        } else {
+          dd[t] = __ldg(depth + p);
+          if (color) {
+            const long long HW = (long long)w.W * w.H;
+            const long long p3 = 2 * w.pix_off + p;
+            cc[t][0] = __ldg(rgb + p3);
+            cc[t][1] = __ldg(rgb + p3 + HW);
+            cc[t][2] = __ldg(rgb + p3 + 2 * HW);
+          }
         }
       }
 #pragma unroll
@@ -113,12 +139,20 @@ __global__ void __launch_bounds__(256) k_tsdf_integrate(const __grid_constant__ 
   }
 }
 
-void launch_tsdf(const BatchDev& b, const TsdfArgs& a, const float* depth, const float* rgb, float* tsdf,
-                 float* weight, float* color, int num_sms, cudaStream_t st) {
+int launch_tsdf(const BatchDev& b, const TsdfArgs& a, const float* depth, const float* rgb, float4* pack_scratch,
+                float* tsdf, float* weight, float* color, int num_sms, cudaStream_t st) {
   const long long nb = (long long)((a.dims[0] + 7) / 8) * ((a.dims[1] + 7) / 8) * ((a.dims[2] + 7) / 8);
-  if (nb <= 0) return;
+  if (nb <= 0) return 0;
+  int launches = 0;
+  const float4* packed = nullptr;
+  if (rgb && pack_scratch) {
+    k_tsdf_pack<<<num_sms * 8, 256, 0, st>>>(b, depth, rgb, pack_scratch);
+    packed = pack_scratch;
+    ++launches;
+  }
   const long long blk = std::min<long long>(nb * 2, (long long)num_sms * 16);
-  k_tsdf_integrate<<<(unsigned)blk, 256, 0, st>>>(b, a, depth, rgb, tsdf, weight, color);
+  k_tsdf_integrate<<<(unsigned)blk, 256, 0, st>>>(b, a, depth, rgb, packed, tsdf, weight, color);
+  return launches + 1;
 }
 
 }  // namespace pgs

@@ -728,9 +728,13 @@ pgs_status pgs_tsdf_integrate(pgs_scene* s, const pgs_camera* cams, int n_views,
   }
   a.voxel = vol->voxel;
   a.trunc = vol->trunc;
+  // the tile-sort buffer ptile_b (sort scratch, free between renders) holds the interleaved maps when it is large
+  // enough (16 B per pixel); otherwise the colour planes are read directly
+  float4* pack = (d_rgb && s->cap_pairs * (long long)sizeof(uint32_t) >= b.total_pixels * (long long)sizeof(float4))
+                     ? reinterpret_cast<float4*>(s->ptile_b)
+                     : nullptr;
   prof_mark(s, PGS_STAGE_TSDF, 0, st);
-  launch_tsdf(b, a, d_depth, d_rgb, d_tsdf, d_weight, d_color, s->num_sms, st);
-  s->launches += 1;
+  s->launches += launch_tsdf(b, a, d_depth, d_rgb, pack, d_tsdf, d_weight, d_color, s->num_sms, st);
   prof_mark(s, PGS_STAGE_TSDF, 1, st);
   PGS_CUDA(cudaGetLastError());
   return PGS_OK;

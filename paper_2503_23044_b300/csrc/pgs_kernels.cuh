@@ -133,8 +133,10 @@ struct TsdfArgs {
   float origin[3], voxel, trunc;
   int dims[3];
 };
-void launch_tsdf(const BatchDev& b, const TsdfArgs& a, const float* depth, const float* rgb, float* tsdf,
-                 float* weight, float* color, int num_sms, cudaStream_t st);
+// pack_scratch: 16 B per pixel of the batch for the interleaved maps, or null (colour fusion then reads the
+// planes); returns the number of launches
+int launch_tsdf(const BatchDev& b, const TsdfArgs& a, const float* depth, const float* rgb, float4* pack_scratch,
+                float* tsdf, float* weight, float* color, int num_sms, cudaStream_t st);
 void launch_prior_filter(const BatchDev& b, const PriorArgs& pa, const float* dp, const float* pts, long long n_pts,
                          float* partials, float* means, float* scale_shift, float* prior_out, float* mask_out,
                          float* err_out, int num_sms, cudaStream_t st);
