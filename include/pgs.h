@@ -397,8 +397,12 @@ pgs_status pgs_ncc_loss_grad(pgs_scene* s, const pgs_camera* cams, int n_views, 
  * NULL too).  Volume state (device, caller-owned, x fastest: linear index
  * (k ny + j) nx + i): d_tsdf and d_weight float[n], d_color float[n][3] or
  * NULL; initialise weight to 0 and tsdf / colour to finite values (0) before
- * the first call; later calls keep fusing.  Errors: PGS_ERR_INVALID_ARG for
- * null pointers, dims < 1 or more than 2^34 voxels, voxel <= 0 or trunc <= 0. */
+ * the first call; later calls keep fusing.  With colour, and when the scene's
+ * pair capacity holds 4 x the batch's pixels, the call first interleaves depth
+ * and colour into the scene's tile-sort scratch (free between renders), so
+ * like every call on a scene it must not overlap another call on the same
+ * scene.  Errors: PGS_ERR_INVALID_ARG for null pointers, dims < 1 or more than
+ * 2^34 voxels, voxel <= 0 or trunc <= 0. */
 typedef struct pgs_tsdf_volume {
   float origin[3];              /* world position of the corner of voxel (0, 0, 0) */
   float voxel;                  /* voxel edge length */

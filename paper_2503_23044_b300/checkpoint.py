@@ -66,8 +66,10 @@ def save(path: str, params: Dict[str, torch.Tensor], render_params: Union[B.Rend
 def load(path: str, device: Union[str, torch.device] = "cuda") -> Dict[str, Any]:
     """Read a checkpoint: dict(step, params (on ``device``), render_params (dict),
     optimizer_state, extra).  Optimiser tensors stay on the CPU; the optimiser's
-    ``load_state_dict`` moves them next to its parameters."""
-    state = torch.load(path, map_location="cpu", weights_only=False)
+    ``load_state_dict`` moves them next to its parameters.  The file is read with
+    torch's weights-only unpickler, so loading runs no code from the file; ``extra``
+    must therefore hold plain values (numbers, strings, lists, tuples, dicts, tensors)."""
+    state = torch.load(path, map_location="cpu", weights_only=True)
     if not isinstance(state, dict) or state.get("format") != FORMAT:
         raise ValueError(f"{path}: not a checkpoint of format {FORMAT}")
     state["params"] = {k: v.to(device) for k, v in state["params"].items()}
